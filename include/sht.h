@@ -1,0 +1,130 @@
+/*
+ * sht.h -- C ABI of a single-GPU (sm_103a) spherical harmonic transform
+ * library following Szydlarski, Esterie, Falcou, Grigori and Stompor,
+ * "Parallel Spherical Harmonic Transforms on heterogeneous architectures
+ * (GPUs/multi-core CPUs)", arXiv:1106.0159.
+ *
+ * Problem statement (Section 2.1, eqs. map2almDef and alm2mapDef; Section 2.2):
+ *   synthesis  s(theta_r, phi_rj) = sum_{l<=lmax} sum_{|m|<=min(l,mmax)} a_lm Y_lm(theta_r, phi_rj)
+ *   analysis   a_lm = sum_r w_r sum_j s(theta_r, phi_rj) conj(Y_lm(theta_r, phi_rj))
+ * with Y_lm = lambda_lm(cos theta) exp(i m phi) (eq. YlmDef), lambda_lm the
+ * normalised associated Legendre functions of eqs. (assLegRec)-(pm1m) without
+ * a Condon-Shortley factor (lambda_mm > 0), a real map, so that
+ * a_{l,-m} = (-1)^m conj(a_lm) and only m >= 0 is stored, and an
+ * iso-latitude grid: ring r has nphi[r] equidistant pixels at
+ * phi_rj = phi0[r] + 2 pi j / nphi[r] (Section 2.2).
+ *
+ * Layouts (all little-endian, no padding):
+ *   alm   complex128 interleaved (re, im), [nmaps][nalm], m-major triangle:
+ *         index(l, m) = m (2 lmax + 3 - m) / 2 + (l - m), 0 <= m <= mmax, m <= l <= lmax.
+ *         Im a_l0 is ignored on input and written as 0 on output.
+ *   map   double, [nmaps][npix], rings in the order given to sht_plan_create,
+ *         pixel j of ring r at offset sum_{r' < r} nphi[r'] + j.
+ *   delta complex128, [nmaps][nrings][mmax + 1]: Delta^A_m(r) of eq. (DeltaDef)
+ *         (synthesis) or Delta^S_m(r) of eq. (almfftdef), weight included
+ *         (analysis); ring order as for maps.
+ *
+ * Ownership and ordering: device pointers are owned by the caller and must
+ * not alias; host arrays passed to the plan are copied.  Every transform call
+ * is asynchronous and stream-ordered on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream).  Arguments are validated before anything is
+ * enqueued; a call that returns an error has enqueued nothing and written
+ * nothing.  A plan owns device tables and a scratch workspace that it grows
+ * on demand; use one plan from one stream at a time.  CUDA failures map to
+ * SHT_ECUDA and the CUDA error text is kept in the plan
+ * (sht_plan_last_error).
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s *sht_plan_t;
+
+typedef enum {
+    SHT_OK = 0,
+    SHT_EINVAL = 1,        /* invalid argument (checked before any device work) */
+    SHT_ENOMEM = 2,        /* host or device allocation failed */
+    SHT_ECUDA = 3,         /* a CUDA call failed; see sht_plan_last_error */
+    SHT_EUNSUPPORTED = 4,  /* valid but outside what this build implements */
+    SHT_ETIMEOUT = 5       /* a bounded device wait gave up */
+} sht_status;
+
+typedef enum {
+    SHT_GRID_CUSTOM = 0,
+    SHT_GRID_HEALPIX = 1,
+    SHT_GRID_GAUSS_LEGENDRE = 2
+} sht_grid;
+
+/*
+ * Create a plan for rings (nphi[r], theta[r], phi0[r], w[r]), r < nrings,
+ * and band limits lmax >= mmax >= 0 (Section 2.2; the weights w_n of
+ * eq. map2almDef are taken per ring and applied to every pixel of the ring).
+ * Host arrays, copied.  Rules: nrings >= 1, 1 <= nphi[r] <= 2^20,
+ * 0 <= theta[r] <= pi, finite phi0 and w, lmax <= 16383.  Rings may come in
+ * any order; rings mirrored about the equator are paired internally
+ * (lambda_lm(-x) = (-1)^(l+m) lambda_lm(x)).  nphi may be smaller than
+ * 2 mmax + 1, in which case the phi sums alias as the definition implies.
+ * `grid` is informational.  Returns SHT_EINVAL for bad arguments,
+ * SHT_ENOMEM / SHT_ECUDA when device set-up fails (nothing is leaked).
+ */
+sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings,
+                           const int64_t *nphi, const double *theta, const double *phi0,
+                           const double *w, int lmax, int mmax);
+
+/* Free the plan, its device tables and workspace (synchronises the device). NULL is ignored. */
+void sht_plan_destroy(sht_plan_t plan);
+
+/*
+ * Synthesis, Algorithm 2 (inverse transform): alm (device, [nmaps][nalm]
+ * complex128) -> map (device, [nmaps][npix] double).  Runs the Legendre
+ * step (eq. DeltaDef via eq. assLegRec) then the ring step (eq. Delta2map).
+ */
+sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream);
+
+/*
+ * Analysis, Algorithm 1 (direct transform): map (device, [nmaps][npix]) ->
+ * alm (device, [nmaps][nalm] complex128).  Runs the ring step (eq. almfftdef)
+ * then the Legendre step (eq. almdef) and a fixed-order reduction over ring
+ * blocks (deterministic: no atomics).
+ */
+sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream);
+
+/* The four stages on their own (same layouts; delta as documented above). */
+sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int nmaps, void *stream); /* eq. DeltaDef */
+sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int nmaps, void *stream);    /* eq. Delta2map */
+sht_status sht_ring_anal(sht_plan_t plan, const double *map, void *delta, int nmaps, void *stream);    /* eq. almfftdef */
+sht_status sht_legendre_anal(sht_plan_t plan, const void *delta, void *alm, int nmaps, void *stream);  /* eq. almdef */
+
+/* Sizes and indexing (pure host functions). */
+int64_t sht_nalm(int lmax, int mmax);                 /* (mmax+1)(lmax+1) - mmax(mmax+1)/2, or -1 if invalid */
+int64_t sht_alm_index(int lmax, int l, int m);        /* m (2 lmax + 3 - m)/2 + (l - m), or -1 if invalid */
+int64_t sht_plan_npix(sht_plan_t plan);
+int     sht_plan_nrings(sht_plan_t plan);
+int     sht_plan_npairs(sht_plan_t plan);            /* ring slots after north/south pairing */
+size_t  sht_workspace_bytes(sht_plan_t plan, int nmaps); /* scratch the transforms need for nmaps maps */
+
+/*
+ * Grid helpers (pure host).  HEALPix (Gorski et al. 2005, the grid of
+ * Section 5): 4 nside - 1 rings north to south, caller arrays of that length,
+ * equal weights 4 pi / (12 nside^2).  Gauss-Legendre: nrings rings at the
+ * roots of P_nrings, north first, nphi pixels each, phi0 = 0,
+ * w = 2 pi w_j / nphi with w_j the Gauss weights.  SHT_EINVAL on bad sizes.
+ */
+sht_status sht_geom_healpix(int nside, int64_t *nphi, double *theta, double *phi0, double *w);
+sht_status sht_geom_gauss_legendre(int nrings, int64_t nphi, int64_t *nphi_out, double *theta,
+                                   double *phi0, double *w);
+
+const char *sht_status_string(sht_status s);
+const char *sht_plan_last_error(sht_plan_t plan);     /* "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

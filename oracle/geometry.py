@@ -11,7 +11,7 @@ published definitions:
   phi0 = pi / (4 Nside) when i - Nside is even and 0 otherwise; the south
   cap mirrors the north one with z -> -z.  Pixels are equal-area, so the
   quadrature weight of every pixel is 4 pi / npix.
-* Gauss-Legendre: the N roots x_j of P_N (scipy), north first, equal nphi,
+* Gauss-Legendre: the N roots x_j of P_N (scipy, Newton-polished), north first, equal nphi,
   phi0 = 0, per-pixel weight 2 pi w_j / nphi with w_j the Gauss weights.
 
 Each builder returns (nphi int64[R], theta float64[R], phi0 float64[R],
@@ -53,14 +53,35 @@ def healpix(nside: int):
     return nphi, theta, phi0, w
 
 
+def _legendre_and_derivative(x, n):
+    """P_n(x) and P_n'(x) by the Bonnet recurrence, in x's dtype."""
+    p0 = np.ones_like(x)
+    p1 = x.copy()
+    for l in range(2, n + 1):
+        p0, p1 = p1, ((2 * l - 1) * x * p1 - (l - 1) * p0) / l
+    if n == 0:
+        return p0, np.zeros_like(x)
+    dp = n * (x * p1 - p0) / (x * x - 1)
+    return p1, dp
+
+
 def gauss_legendre(nrings: int, nphi: int):
     from scipy.special import roots_legendre
 
-    x, wg = roots_legendre(int(nrings))
+    n = int(nrings)
+    x0, _ = roots_legendre(n)
+    # scipy's nodes, polished by two Newton steps in long double (scipy's weights for
+    # n in the thousands are only good to ~1e-13); weights 2 / ((1 - x^2) P_n'(x)^2)
+    x = x0.astype(np.longdouble)
+    for _ in range(2):
+        p, dp = _legendre_and_derivative(x, n)
+        x = x - p / dp
+    _, dp = _legendre_and_derivative(x, n)
+    wg = 2 / ((1 - x * x) * dp * dp)
     order = np.argsort(-x)  # north (x = cos theta near +1) first
     x = x[order]
-    wg = wg[order]
-    theta = np.arccos(x)
+    wg = wg[order].astype(np.float64)
+    theta = np.arccos(x).astype(np.float64)
     nphi_a = np.full(int(nrings), int(nphi), dtype=np.int64)
     phi0 = np.zeros(int(nrings), dtype=np.float64)
     w = 2.0 * np.pi * wg / float(nphi)

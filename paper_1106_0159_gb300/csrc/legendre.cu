@@ -1,0 +1,505 @@
+// Legendre stage of the transforms (Section 2.2 eqs. DeltaDef and almdef,
+// Algorithms 1-2 step "core calculation", GPU form of Algorithms 5-6).
+//
+// Both kernels run one CTA per (m, block of ring slots), m ascending so the
+// longest l-ranges start first.  A ring slot is a ring in the northern
+// hemisphere together with its mirror ring (theta, pi - theta); one thread
+// runs the l-recurrence once for both, using
+// lambda_lm(-x) = (-1)^(l+m) lambda_lm(x): terms with l+m even are summed
+// into E, odd ones into O, and Delta_N = E + O, Delta_S = E - O.
+//
+// The recurrence of eq. (assLegRec) (with the sign reading
+// lambda_l = beta_l (x lambda_{l-1} - lambda_{l-2} / beta_{l-1})) is run in
+// the normalised variable y_l = lambda_l / c_l, where c_m = c_{m+1} = 1 and
+// c_l = (beta_l / beta_{l-1}) c_{l-2}.  Then
+//     y_l = alpha_l x y_{l-1} - y_{l-2},   alpha_l = beta_l c_{l-1} / c_l,
+// which costs two FP64 instructions per step: t = x y_{l-1} is formed as
+// fma(-u, y, y) with u = 1 - cos(theta) (exact near the poles, where
+// cos(theta) rounded to double would displace the ring by ~1e-16/sin(theta)),
+// then y_l = fma(alpha_l, t, -y_{l-2}).  The factor c_l is folded into a_lm
+// when it is staged (synthesis) or applied after the ring reduction
+// (analysis).  The coefficient table stores mu_m at l = m and sqrt(2m+3)
+// (eq. pm1m) at l = m + 1; seeding y_{m-1} = 0, y_{m-2} = -y_m lets the same
+// step produce y_m and y_{m+1}.
+//
+// Rescaling (the scheme Section 2.1 leaves to HEALPix/S2HAT): the start
+// value mu_m sin^m(theta) is formed by binary powering with its binary
+// exponent carried in an int and split as y * 2^(512 k), k <= 0.  While
+// k < 0 the pair (y_l, y_{l-1}) is multiplied by 2^-512 (k += 1) whenever
+// its exponent passes 2^256; the test reads the exponent bits (integer pipe)
+// once every 16 steps.  Terms are accumulated only at k = 0; terms with
+// k < 0 are below 2^-224 and are dropped.  Once a whole warp has k = 0 the
+// loop carries no tests at all.
+#include "sht_internal.h"
+
+#include <algorithm>
+
+namespace sht {
+namespace {
+
+constexpr int SYN_T = 128;      // threads (= ring slots) per synthesis CTA
+constexpr int ANA_T = 128;      // threads per analysis CTA
+constexpr int CHL = 128;        // l-values staged per shared-memory chunk (multiple of 16)
+constexpr int SUB = 16;         // steps between rescale tests
+constexpr int RESCALE_THR = 1023 + 256;  // biased exponent that triggers a rescale
+constexpr int RED_CL = 8;       // l-values per warp reduction round (analysis)
+
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+// v in [1, 2) times 2^e  <-  v (positive, normal)
+__device__ __forceinline__ void normalise(double &v, int &e)
+{
+    int hi = __double2hiint(v);
+    e += ((hi >> 20) & 0x7ff) - 1023;
+    hi = (hi & 0x800fffff) | (1023 << 20);
+    v = __hiloint2double(hi, __double2loint(v));
+}
+
+__device__ __forceinline__ double pow2i(int e)  // 2^e for -1022 <= e <= 1023
+{
+    return __hiloint2double((e + 1023) << 20, 0);
+}
+
+// lambda_mm = mu_m sin^m(theta) as y0 * 2^(512 k) with y0 <= mu_m
+__device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
+{
+    if (m > 0 && !(s > 1e-300)) {  // pole: lambda_lm = 0 for m > 0
+        y0 = 0.0;
+        k = 0;
+        return;
+    }
+    double r = 1.0;
+    int er = 0;
+    double b = s;
+    int eb = 0;
+    if (m > 0) normalise(b, eb);
+    for (int mm = m; mm; mm >>= 1) {
+        if (mm & 1) {
+            r *= b;
+            er += eb;
+            normalise(r, er);
+        }
+        if (mm > 1) {
+            b *= b;
+            eb *= 2;
+            normalise(b, eb);
+        }
+    }
+    // r * 2^er, r in [1, 2), er <= 0;  k = ceil(er / 512)
+    int kk = (er >= 0) ? 0 : -((-er) >> 9);
+    int rem = er - 512 * kk;  // in (-512, 0]
+    y0 = mu * r * pow2i(rem);
+    k = kk;
+}
+
+struct SynArgs {
+    const double2 *alm;   // [nmaps][nalm], first map of this launch
+    double2 *delta;       // [nmaps][nrings][mmax+1]
+    const int *slotN, *slotS;
+    const double *u, *s;
+    const double *alpha, *cfac;
+    int nslots, nblk, lmax, mmax, nrings;
+    int64_t nalm;
+};
+
+template <int NM>
+__global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
+{
+    __shared__ double s_al[CHL];
+    __shared__ double2 s_a[NM][CHL];
+
+    const int m = blockIdx.x / A.nblk;
+    const int blk = blockIdx.x - m * A.nblk;
+    const int slot = blk * SYN_T + threadIdx.x;
+    const bool active = slot < A.nslots;
+    const int L = A.lmax;
+    const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;  // index(m, m)
+
+    double u = 0.0, y1 = 0.0, y2 = 0.0;
+    int k = 0;
+    if (active) {
+        u = A.u[slot];
+        double y0;
+        sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
+        y1 = 0.0;     // y_{m-1}
+        y2 = -y0;     // y_{m-2} := -y_m, so the first step yields y_m
+    }
+
+    double Er[NM], Ei[NM], Or[NM], Oi[NM];
+#pragma unroll
+    for (int g = 0; g < NM; ++g) Er[g] = Ei[g] = Or[g] = Oi[g] = 0.0;
+
+    for (int l0 = m; l0 <= L; l0 += CHL) {
+        const int nl = min(CHL, L - l0 + 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nl; i += SYN_T) {
+            const int64_t ix = base + (l0 - m) + i;
+            s_al[i] = A.alpha[ix];
+            const double c = A.cfac[ix];
+#pragma unroll
+            for (int g = 0; g < NM; ++g) {
+                double2 a = A.alm[(int64_t)g * A.nalm + ix];
+                s_a[g][i] = make_double2(c * a.x, m == 0 ? 0.0 : c * a.y);
+            }
+        }
+        __syncthreads();
+
+        for (int j0 = 0; j0 < nl; j0 += SUB) {
+            const int jn = min(j0 + SUB, nl);
+            const bool scaled = __any_sync(0xffffffffu, k < 0);
+            if (!scaled) {
+                int j = j0;
+                for (; j + 1 < jn; j += 2) {
+                    double t = fma(-u, y1, y1);
+                    double y = fma(s_al[j], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+#pragma unroll
+                    for (int g = 0; g < NM; ++g) {
+                        const double2 a = s_a[g][j];
+                        Er[g] = fma(a.x, y, Er[g]);
+                        Ei[g] = fma(a.y, y, Ei[g]);
+                    }
+                    t = fma(-u, y1, y1);
+                    y = fma(s_al[j + 1], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+#pragma unroll
+                    for (int g = 0; g < NM; ++g) {
+                        const double2 a = s_a[g][j + 1];
+                        Or[g] = fma(a.x, y, Or[g]);
+                        Oi[g] = fma(a.y, y, Oi[g]);
+                    }
+                }
+                if (j < jn) {  // ragged end: one even step
+                    double t = fma(-u, y1, y1);
+                    double y = fma(s_al[j], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+#pragma unroll
+                    for (int g = 0; g < NM; ++g) {
+                        const double2 a = s_a[g][j];
+                        Er[g] = fma(a.x, y, Er[g]);
+                        Ei[g] = fma(a.y, y, Ei[g]);
+                    }
+                }
+            } else {
+                const bool any_live = __any_sync(0xffffffffu, active && k == 0);
+                for (int j = j0; j < jn; ++j) {
+                    double t = fma(-u, y1, y1);
+                    double y = fma(s_al[j], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+                    if (any_live) {
+                        const double ya = (k == 0) ? y : 0.0;
+                        if (((j + l0 - m) & 1) == 0) {
+#pragma unroll
+                            for (int g = 0; g < NM; ++g) {
+                                const double2 a = s_a[g][j];
+                                Er[g] = fma(a.x, ya, Er[g]);
+                                Ei[g] = fma(a.y, ya, Ei[g]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < NM; ++g) {
+                                const double2 a = s_a[g][j];
+                                Or[g] = fma(a.x, ya, Or[g]);
+                                Oi[g] = fma(a.y, ya, Oi[g]);
+                            }
+                        }
+                    }
+                }
+                if (k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                    y1 *= 0x1p-512;
+                    y2 *= 0x1p-512;
+                    k += 1;
+                }
+            }
+        }
+    }
+
+    if (active) {
+        const int rn = A.slotN[slot], rs = A.slotS[slot];
+        const int64_t mstride = A.mmax + 1;
+#pragma unroll
+        for (int g = 0; g < NM; ++g) {
+            double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+            if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(Er[g] + Or[g], Ei[g] + Oi[g]);
+            if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(Er[g] - Or[g], Ei[g] - Oi[g]);
+        }
+    }
+}
+
+struct AnaArgs {
+    const double2 *delta;  // [nmaps][nrings][mmax+1], first map of this launch
+    double2 *partial;      // [nblk][nmaps_total][nalm]
+    const int *slotN, *slotS;
+    const double *u, *s;
+    const double *alpha;
+    int nslots, nblk, lmax, mmax, nrings;
+    int64_t nalm;
+    int64_t part_map_stride;   // nalm
+    int64_t part_blk_stride;   // nmaps_total * nalm
+};
+
+// Reduce-scatter of RED_CL values per lane over the warp: afterwards every lane
+// holds the warp total of value (lane & (RED_CL-1)).
+__device__ __forceinline__ double warp_reduce_scatter8(double v[RED_CL])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = RED_CL / 2; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? v[i] : v[i + h];
+            const double keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    double r = v[0];
+    r += __shfl_xor_sync(0xffffffffu, r, 8);
+    r += __shfl_xor_sync(0xffffffffu, r, 16);
+    return r;
+}
+
+template <int NM, int K>
+__global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
+{
+    constexpr int NW = ANA_T / 32;
+    __shared__ double s_al[CHL];
+    __shared__ double s_red[NW][CHL][2 * NM];
+
+    const int m = blockIdx.x / A.nblk;
+    const int blk = blockIdx.x - m * A.nblk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = A.lmax;
+    const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
+    const int64_t mstride = A.mmax + 1;
+
+    double u[K], y1[K], y2[K];
+    int k[K];
+    double Sr[K][NM], Si[K][NM], Dr[K][NM], Di[K][NM];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int slot = blk * (ANA_T * K) + q * ANA_T + threadIdx.x;
+        u[q] = 0.0;
+        y1[q] = 0.0;
+        y2[q] = 0.0;
+        k[q] = 0;
+#pragma unroll
+        for (int g = 0; g < NM; ++g) Sr[q][g] = Si[q][g] = Dr[q][g] = Di[q][g] = 0.0;
+        if (slot < A.nslots) {
+            u[q] = A.u[slot];
+            double y0;
+            sectoral_start(A.s[slot], A.alpha[base], m, y0, k[q]);
+            y2[q] = -y0;
+            const int rn = A.slotN[slot], rs = A.slotS[slot];
+#pragma unroll
+            for (int g = 0; g < NM; ++g) {
+                const double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+                double2 dn = make_double2(0.0, 0.0), ds = make_double2(0.0, 0.0);
+                if (rn >= 0) dn = d[(int64_t)rn * mstride + m];
+                if (rs >= 0) ds = d[(int64_t)rs * mstride + m];
+                Sr[q][g] = dn.x + ds.x;
+                Si[q][g] = dn.y + ds.y;
+                Dr[q][g] = dn.x - ds.x;
+                Di[q][g] = dn.y - ds.y;
+            }
+        }
+    }
+
+    for (int l0 = m; l0 <= L; l0 += CHL) {
+        const int nl = min(CHL, L - l0 + 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nl; i += ANA_T) s_al[i] = A.alpha[base + (l0 - m) + i];
+        __syncthreads();
+
+        for (int j0 = 0; j0 < nl; j0 += SUB) {
+            bool scaled = false;
+#pragma unroll
+            for (int q = 0; q < K; ++q) scaled |= (k[q] < 0);
+            scaled = __any_sync(0xffffffffu, scaled);
+            // two rounds of RED_CL l-values per SUB block
+#pragma unroll
+            for (int h = 0; h < SUB / RED_CL; ++h) {
+                const int jb = j0 + h * RED_CL;
+                double vr[NM][RED_CL], vi[NM][RED_CL];
+#pragma unroll
+                for (int jj = 0; jj < RED_CL; ++jj) {
+                    const int j = jb + jj;
+                    const double al = (j < nl) ? s_al[j] : 0.0;
+                    const bool even = ((jj & 1) == 0);  // jb - 0 is even: l0 - m and j0, jb are even
+#pragma unroll
+                    for (int g = 0; g < NM; ++g) vr[g][jj] = vi[g][jj] = 0.0;
+#pragma unroll
+                    for (int q = 0; q < K; ++q) {
+                        const double t = fma(-u[q], y1[q], y1[q]);
+                        double y = fma(al, t, -y2[q]);
+                        if (j >= nl) y = y1[q] * 0.0;  // past the end: keep the state (no-op step)
+                        if (j < nl) {
+                            y2[q] = y1[q];
+                            y1[q] = y;
+                        }
+                        if (scaled) y = (k[q] == 0) ? y : 0.0;
+#pragma unroll
+                        for (int g = 0; g < NM; ++g) {
+                            vr[g][jj] = fma(y, even ? Sr[q][g] : Dr[q][g], vr[g][jj]);
+                            vi[g][jj] = fma(y, even ? Si[q][g] : Di[q][g], vi[g][jj]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < NM; ++g) {
+                    const double rr = warp_reduce_scatter8(vr[g]);
+                    const double ri = warp_reduce_scatter8(vi[g]);
+                    if (lane < RED_CL && jb + lane < CHL) {
+                        s_red[warp][jb + lane][2 * g] = rr;
+                        s_red[warp][jb + lane][2 * g + 1] = ri;
+                    }
+                }
+            }
+            if (scaled) {
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    if (k[q] < 0 && max(dexp(y1[q]), dexp(y2[q])) > RESCALE_THR) {
+                        y1[q] *= 0x1p-512;
+                        y2[q] *= 0x1p-512;
+                        k[q] += 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // sum the warps and write this block's partial a_lm (times 1/c, applied later)
+        for (int i = threadIdx.x; i < nl * NM; i += ANA_T) {
+            const int j = i % nl, g = i / nl;
+            double re = 0.0, im = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                re += s_red[w][j][2 * g];
+                im += s_red[w][j][2 * g + 1];
+            }
+            A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + base + (l0 - m) + j] =
+                make_double2(re, im);
+        }
+    }
+}
+
+// a_lm = c_lm * sum over ring blocks (fixed order), Im a_l0 = 0
+__global__ void reduce_blocks_kernel(const double2 *__restrict__ partial, const double *__restrict__ cfac,
+                                     double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
+                                     int64_t blk_stride)
+{
+    const int64_t total = nalm * nmaps;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / nalm, i = t - g * nalm;
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            const double2 v = partial[b * blk_stride + g * nalm + i];
+            re += v.x;
+            im += v.y;
+        }
+        const double c = cfac[i];
+        alm[t] = make_double2(c * re, i <= lmax ? 0.0 : c * im);
+    }
+}
+
+int anal_slots_per_cta(const Plan &p) { return p.nslots >= 4 * ANA_T ? 4 * ANA_T : ANA_T; }
+
+}  // namespace
+
+cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st)
+{
+    SynArgs A;
+    A.slotN = p.d_slotN;
+    A.slotS = p.d_slotS;
+    A.u = p.d_u;
+    A.s = p.d_s;
+    A.alpha = p.d_alpha;
+    A.cfac = p.d_cfac;
+    A.nslots = p.nslots;
+    A.nblk = (p.nslots + SYN_T - 1) / SYN_T;
+    A.lmax = p.lmax;
+    A.mmax = p.mmax;
+    A.nrings = p.nrings;
+    A.nalm = p.nalm;
+    const unsigned grid = (unsigned)((p.mmax + 1) * A.nblk);
+    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    int g0 = 0;
+    while (g0 < nmaps) {
+        const int left = nmaps - g0;
+        A.alm = alm + (int64_t)g0 * p.nalm;
+        A.delta = delta + (int64_t)g0 * dstride;
+        if (left >= 4) {
+            legendre_synth_kernel<4><<<grid, SYN_T, 0, st>>>(A);
+            g0 += 4;
+        } else if (left >= 2) {
+            legendre_synth_kernel<2><<<grid, SYN_T, 0, st>>>(A);
+            g0 += 2;
+        } else {
+            legendre_synth_kernel<1><<<grid, SYN_T, 0, st>>>(A);
+            g0 += 1;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+size_t legendre_anal_partial_bytes(const Plan &p, int nmaps)
+{
+    const int per = anal_slots_per_cta(p);
+    const int nblk = (p.nslots + per - 1) / per;
+    return (size_t)nblk * (size_t)nmaps * (size_t)p.nalm * sizeof(double2);
+}
+
+cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
+                                 cudaStream_t st)
+{
+    const int per = anal_slots_per_cta(p);
+    AnaArgs A;
+    A.slotN = p.d_slotN;
+    A.slotS = p.d_slotS;
+    A.u = p.d_u;
+    A.s = p.d_s;
+    A.alpha = p.d_alpha;
+    A.nslots = p.nslots;
+    A.nblk = (p.nslots + per - 1) / per;
+    A.lmax = p.lmax;
+    A.mmax = p.mmax;
+    A.nrings = p.nrings;
+    A.nalm = p.nalm;
+    A.part_map_stride = p.nalm;
+    A.part_blk_stride = (int64_t)nmaps * p.nalm;
+    const unsigned grid = (unsigned)((p.mmax + 1) * A.nblk);
+    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    int g0 = 0;
+    while (g0 < nmaps) {
+        const int left = nmaps - g0;
+        A.delta = delta + (int64_t)g0 * dstride;
+        A.partial = partial + (int64_t)g0 * p.nalm;
+        if (left >= 2) {
+            if (per == 4 * ANA_T)
+                legendre_anal_kernel<2, 4><<<grid, ANA_T, 0, st>>>(A);
+            else
+                legendre_anal_kernel<2, 1><<<grid, ANA_T, 0, st>>>(A);
+            g0 += 2;
+        } else {
+            if (per == 4 * ANA_T)
+                legendre_anal_kernel<1, 4><<<grid, ANA_T, 0, st>>>(A);
+            else
+                legendre_anal_kernel<1, 1><<<grid, ANA_T, 0, st>>>(A);
+            g0 += 1;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t total = p.nalm * nmaps;
+    int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    reduce_blocks_kernel<<<rgrid, 256, 0, st>>>(partial, p.d_cfac, alm, A.nblk, p.nalm, nmaps, p.lmax,
+                                                A.part_blk_stride);
+    return cudaGetLastError();
+}
+
+}  // namespace sht

@@ -1,0 +1,537 @@
+// Ring stage of the transforms (Section 2.2 eqs. Delta2map and almfftdef,
+// the FFT steps of Algorithms 1-2).
+//
+// Every pixel ring is a real sequence of nphi equidistant samples starting at
+// phi0.  Two rings of equal length (normally a north/south mirror pair) share
+// one complex DFT: ring A on the real part, ring B on the imaginary part.
+//
+// synthesis:  v_m = Delta_m exp(i m phi0) for 0 <= m <= mmax, folded into the
+//             nphi bins (bin m mod nphi, and conj(v_m) into bin -m mod nphi),
+//             then z_j = sum_k Z_k exp(+2 pi i j k / nphi).
+// analysis:   S_k = sum_j s_j exp(-2 pi i j k / nphi),
+//             Delta^S_m = w exp(-i m phi0) S_(m mod nphi).
+//
+// Each complex DFT is run by one CTA of a persistent grid in three
+// CTA-private scratch buffers: Stockham passes of radix 4, 2, 3, 5, 7, 11 or
+// 13 when nphi factors into those, otherwise Bluestein's chirp-z form with a
+// power-of-two convolution.  The minus-sign DFT is taken as
+// conj(DFT+(conj(x))).  Twiddles, chirps and Bluestein filters are plan
+// tables built on the device at plan creation.
+#include "sht_internal.h"
+
+#include <algorithm>
+#include <map>
+
+namespace sht {
+namespace {
+
+constexpr int FFT_T = 256;
+constexpr int MAXR = 13;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+// One Stockham pass: sub-transforms of length Lsub become length Lsub * p.
+// Input  X[j * (n / Lsub) + q],  j < Lsub, q < n / Lsub
+// Output Y[k * (n / (Lsub p)) + q'], k < Lsub p
+__device__ void stockham_pass(const double2 *__restrict__ X, double2 *__restrict__ Y, int n, int Lsub, int p,
+                              const double2 *__restrict__ tw)
+{
+    const int nq = n / (Lsub * p);
+    const int nbf = Lsub * nq;
+    const int inStride = n / Lsub;
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+        const int k1 = b / nq;
+        const int q = b - k1 * nq;
+        const double2 *src = X + (int64_t)k1 * inStride + q;
+        double2 *dst = Y + (int64_t)k1 * nq + q;
+        const int64_t ostride = (int64_t)Lsub * nq;
+        if (p == 4) {
+            double2 a0 = src[0], a1 = src[nq], a2 = src[2 * nq], a3 = src[3 * nq];
+            if (k1) {
+                const int t = k1 * nq;
+                a1 = cmul(a1, tw[t]);
+                a2 = cmul(a2, tw[2 * t]);
+                a3 = cmul(a3, tw[3 * t]);
+            }
+            const double2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+            const double2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+            const double2 id13 = make_double2(-d13.y, d13.x);  // i * (a1 - a3)
+            dst[0] = cadd(s02, s13);
+            dst[ostride] = cadd(d02, id13);
+            dst[2 * ostride] = csub(s02, s13);
+            dst[3 * ostride] = csub(d02, id13);
+        } else if (p == 2) {
+            double2 a0 = src[0], a1 = src[nq];
+            if (k1) a1 = cmul(a1, tw[k1 * nq]);
+            dst[0] = cadd(a0, a1);
+            dst[ostride] = csub(a0, a1);
+        } else {
+            double2 a[MAXR];
+            a[0] = src[0];
+            for (int r = 1; r < p; ++r) {
+                a[r] = src[(int64_t)r * nq];
+                if (k1) a[r] = cmul(a[r], tw[(int64_t)r * k1 * nq]);
+            }
+            const int wstep = n / p;  // exp(2 pi i / p) = tw[n / p]
+            for (int k2 = 0; k2 < p; ++k2) {
+                double2 acc = a[0];
+                int e = 0;
+                for (int r = 1; r < p; ++r) {
+                    e += k2;
+                    if (e >= p) e -= p;
+                    acc = cadd(acc, cmul(a[r], tw[(int64_t)e * wstep]));
+                }
+                dst[(int64_t)k2 * ostride] = acc;
+            }
+        }
+    }
+}
+
+// Length-n DFT with the + sign on B0[0, n) (all threads of the CTA).  Returns
+// the buffer that holds the result.  B1, B2 hold at least max(n, M) entries.
+__device__ double2 *cta_dft(const FftLen &F, const double2 *__restrict__ tab, double2 *B0, double2 *B1, double2 *B2)
+{
+    if (F.M == 0) {
+        double2 *X = B0, *Y = B1;
+        int Lsub = 1;
+        for (int f = 0; f < F.nfac; ++f) {
+            __syncthreads();
+            stockham_pass(X, Y, F.n, Lsub, F.fac[f], tab + F.tw);
+            double2 *t = X;
+            X = Y;
+            Y = t;
+            Lsub *= F.fac[f];
+        }
+        __syncthreads();
+        return X;
+    }
+    const int n = F.n, M = F.M;
+    const double2 *ch = tab + F.chirp;
+    const double2 *filt = tab + F.filt;
+    for (int j = threadIdx.x; j < M; j += blockDim.x)
+        B1[j] = (j < n) ? cmul(B0[j], ch[j]) : make_double2(0.0, 0.0);
+    double2 *X = B1, *Y = B2;
+    int Lsub = 1;
+    for (int f = 0; f < F.nfac; ++f) {
+        __syncthreads();
+        stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+        double2 *t = X;
+        X = Y;
+        Y = t;
+        Lsub *= F.fac[f];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) X[j] = conjd(cmul(X[j], filt[j]));
+    Lsub = 1;
+    for (int f = 0; f < F.nfac; ++f) {
+        __syncthreads();
+        stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+        double2 *t = X;
+        X = Y;
+        Y = t;
+        Lsub *= F.fac[f];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) B0[k] = cmul(conjd(X[k]), ch[k]);
+    __syncthreads();
+    return B0;
+}
+
+struct RingArgs {
+    const FftItem *items;
+    const FftLen *lens;
+    const double2 *tab;
+    const double2 *phase;   // [nrings][mmax+1]
+    const int64_t *ofs;
+    const double *w;
+    double2 *scratch;       // [grid][3][maxlen]
+    int maxlen;
+    int nitems, nmaps, nrings, mmax;
+    int64_t npix;
+    const double2 *delta_in;   // synthesis input
+    double *map_out;           // synthesis output
+    const double *map_in;      // analysis input
+    double2 *delta_out;        // analysis output
+};
+
+// folded, phased spectrum bin k of one ring
+__device__ __forceinline__ double2 fold_bin(const double2 *__restrict__ d, const double2 *__restrict__ ph, int k, int n,
+                                            int mmax)
+{
+    double2 c = make_double2(0.0, 0.0);
+    for (int m = k; m <= mmax; m += n) c = cadd(c, cmul(d[m], ph[m]));
+    int m0 = (n - k) % n;
+    if (m0 == 0) m0 = n;
+    for (int m = m0; m <= mmax; m += n) c = cadd(c, conjd(cmul(d[m], ph[m])));
+    return c;
+}
+
+__global__ void __launch_bounds__(FFT_T) ring_synth_kernel(RingArgs A)
+{
+    double2 *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
+    double2 *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
+    const int64_t mstride = A.mmax + 1;
+    const int nunits = A.nitems * A.nmaps;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int item = unit / A.nmaps, g = unit - item * A.nmaps;
+        const FftItem it = A.items[item];
+        const FftLen &F = A.lens[it.len_id];
+        const int n = it.n;
+        const double2 *dA = A.delta_in + ((int64_t)g * A.nrings + it.ringA) * mstride;
+        const double2 *pA = A.phase + (int64_t)it.ringA * mstride;
+        const double2 *dB = it.ringB >= 0 ? A.delta_in + ((int64_t)g * A.nrings + it.ringB) * mstride : nullptr;
+        const double2 *pB = it.ringB >= 0 ? A.phase + (int64_t)it.ringB * mstride : nullptr;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const double2 ca = fold_bin(dA, pA, k, n, A.mmax);
+            double2 z = ca;
+            if (dB) {
+                const double2 cb = fold_bin(dB, pB, k, n, A.mmax);
+                z = make_double2(ca.x - cb.y, ca.y + cb.x);  // C_A + i C_B
+            }
+            B0[k] = z;
+        }
+        __syncthreads();
+        const double2 *X = cta_dft(F, A.tab, B0, B1, B2);
+        double *outA = A.map_out + (int64_t)g * A.npix + A.ofs[it.ringA];
+        double *outB = it.ringB >= 0 ? A.map_out + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double2 z = X[j];
+            outA[j] = z.x;
+            if (outB) outB[j] = z.y;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(FFT_T) ring_anal_kernel(RingArgs A)
+{
+    double2 *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
+    double2 *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
+    const int64_t mstride = A.mmax + 1;
+    const int nunits = A.nitems * A.nmaps;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int item = unit / A.nmaps, g = unit - item * A.nmaps;
+        const FftItem it = A.items[item];
+        const FftLen &F = A.lens[it.len_id];
+        const int n = it.n;
+        const double *sA = A.map_in + (int64_t)g * A.npix + A.ofs[it.ringA];
+        const double *sB = it.ringB >= 0 ? A.map_in + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            B0[j] = make_double2(sA[j], sB ? -sB[j] : 0.0);  // conj(s_A + i s_B)
+        __syncthreads();
+        const double2 *X = cta_dft(F, A.tab, B0, B1, B2);  // conj(S)
+        const double2 *pA = A.phase + (int64_t)it.ringA * mstride;
+        double2 *oA = A.delta_out + ((int64_t)g * A.nrings + it.ringA) * mstride;
+        const double wA = A.w[it.ringA];
+        if (it.ringB < 0) {
+            for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
+                const double2 S = conjd(X[m % n]);
+                const double2 v = cmul(conjd(pA[m]), S);
+                oA[m] = make_double2(wA * v.x, m == 0 ? 0.0 : wA * v.y);
+            }
+        } else {
+            const double2 *pB = A.phase + (int64_t)it.ringB * mstride;
+            double2 *oB = A.delta_out + ((int64_t)g * A.nrings + it.ringB) * mstride;
+            const double wB = A.w[it.ringB];
+            for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
+                const int k = m % n;
+                const int kc = (n - k) % n;
+                const double2 S = conjd(X[k]);
+                const double2 Sc = X[kc];  // conj(S_{-k})
+                const double2 SA = make_double2(0.5 * (S.x + Sc.x), 0.5 * (S.y + Sc.y));
+                const double2 D = csub(S, Sc);
+                const double2 SB = make_double2(0.5 * D.y, -0.5 * D.x);  // D / (2 i)
+                const double2 va = cmul(conjd(pA[m]), SA);
+                const double2 vb = cmul(conjd(pB[m]), SB);
+                oA[m] = make_double2(wA * va.x, m == 0 ? 0.0 : wA * va.y);
+                oB[m] = make_double2(wB * vb.x, m == 0 ? 0.0 : wB * vb.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- plan tables
+
+struct TabJob {
+    int64_t off;
+    int n;
+    int kind;  // 0: exp(2 pi i k / n), k < n; 1: chirp exp(i pi j^2 / n), j < n
+};
+
+__global__ void fill_tables_kernel(const TabJob *jobs, int njobs, double2 *tab)
+{
+    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+        const TabJob J = jobs[jb];
+        for (int k = threadIdx.x; k < J.n; k += blockDim.x) {
+            double s, c;
+            if (J.kind == 0) {
+                sincospi(2.0 * (double)k / (double)J.n, &s, &c);
+            } else {
+                const int64_t q = ((int64_t)k * k) % (2 * (int64_t)J.n);
+                sincospi((double)q / (double)J.n, &s, &c);
+            }
+            tab[J.off + k] = make_double2(c, s);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FFT_T) bluestein_filter_kernel(const FftLen *lens, const int *ids, int nids,
+                                                                 double2 *tab, double2 *scratch, int maxlen)
+{
+    double2 *B0 = scratch + (int64_t)blockIdx.x * 3 * maxlen;
+    double2 *B1 = B0 + maxlen, *B2 = B1 + maxlen;
+    for (int t = blockIdx.x; t < nids; t += gridDim.x) {
+        const FftLen &F = lens[ids[t]];
+        const int n = F.n, M = F.M;
+        const double2 *ch = tab + F.chirp;
+        // h'_d = conj(c_d) for 0 <= d < n, h'_{M-d} = conj(c_d) for 0 < d < n
+        for (int j = threadIdx.x; j < M; j += blockDim.x) {
+            double2 v = make_double2(0.0, 0.0);
+            if (j < n)
+                v = conjd(ch[j]);
+            else if (j > M - n)
+                v = conjd(ch[M - j]);
+            B0[j] = v;
+        }
+        __syncthreads();
+        double2 *X = B0, *Y = B1;
+        int Lsub = 1;
+        for (int f = 0; f < F.nfac; ++f) {
+            __syncthreads();
+            stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+            double2 *tmp = X;
+            X = Y;
+            Y = tmp;
+            Lsub *= F.fac[f];
+        }
+        __syncthreads();
+        const double inv = 1.0 / (double)M;
+        for (int j = threadIdx.x; j < M; j += blockDim.x) {
+            const double2 v = X[j];
+            tab[F.filt + j] = make_double2(v.x * inv, v.y * inv);
+        }
+        __syncthreads();
+    }
+    (void)B2;
+}
+
+// exp(i m phi0_r), with m phi0 reduced modulo 2 pi in extra precision
+__global__ void phase_table_kernel(const double *phi0, int nrings, int mmax, double2 *phase)
+{
+    const double TWO_PI_HI = 6.283185307179586232;      // 2 pi rounded to double
+    const double TWO_PI_LO = 2.4492935982947064e-16;     // 2 pi - TWO_PI_HI
+    const int64_t total = (int64_t)nrings * (mmax + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / (mmax + 1));
+        const int m = (int)(t - (int64_t)r * (mmax + 1));
+        const double p = phi0[r];
+        const double hi = (double)m * p;
+        const double lo = fma((double)m, p, -hi);          // m p = hi + lo exactly
+        const double kq = rint(hi / TWO_PI_HI);
+        double red = fma(-kq, TWO_PI_HI, hi);               // exact for |kq| < 2^20
+        red = fma(-kq, TWO_PI_LO, red) + lo;
+        double s, c;
+        sincos(red, &s, &c);
+        phase[t] = make_double2(c, s);
+    }
+}
+
+bool factor_smooth(int n, std::vector<int> &fac)
+{
+    fac.clear();
+    int r = n;
+    while (r % 4 == 0) {
+        fac.push_back(4);
+        r /= 4;
+    }
+    while (r % 2 == 0) {
+        fac.push_back(2);
+        r /= 2;
+    }
+    for (int p : {3, 5, 7, 11, 13}) {
+        while (r % p == 0) {
+            fac.push_back(p);
+            r /= p;
+        }
+    }
+    return r == 1;
+}
+
+}  // namespace
+
+size_t ring_scratch_bytes(const Plan &p) { return (size_t)ring_grid(p) * 3 * (size_t)p.fft_maxlen * sizeof(double2); }
+
+int ring_grid(const Plan &p) { return std::max(1, std::min(p.nitems, 2 * 152)); }
+
+cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
+                              cudaStream_t st)
+{
+    RingArgs A{};
+    A.items = p.d_items;
+    A.lens = p.d_lens;
+    A.tab = p.d_fft_tab;
+    A.phase = p.d_phase;
+    A.ofs = p.d_ofs;
+    A.w = p.d_w;
+    A.scratch = scratch;
+    A.maxlen = p.fft_maxlen;
+    A.nitems = p.nitems;
+    A.nmaps = nmaps;
+    A.nrings = p.nrings;
+    A.mmax = p.mmax;
+    A.npix = p.npix;
+    A.delta_in = delta;
+    A.map_out = map;
+    ring_synth_kernel<<<ring_grid(p), FFT_T, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring_anal(const Plan &p, const double *map, double2 *delta, double2 *scratch, int nmaps,
+                             cudaStream_t st)
+{
+    RingArgs A{};
+    A.items = p.d_items;
+    A.lens = p.d_lens;
+    A.tab = p.d_fft_tab;
+    A.phase = p.d_phase;
+    A.ofs = p.d_ofs;
+    A.w = p.d_w;
+    A.scratch = scratch;
+    A.maxlen = p.fft_maxlen;
+    A.nitems = p.nitems;
+    A.nmaps = nmaps;
+    A.nrings = p.nrings;
+    A.mmax = p.mmax;
+    A.npix = p.npix;
+    A.map_in = map;
+    A.delta_out = delta;
+    ring_anal_kernel<<<ring_grid(p), FFT_T, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t build_phase_table(Plan &p)
+{
+    cudaError_t e;
+    double *d_phi0 = nullptr;
+    const size_t bytes = (size_t)p.nrings * (p.mmax + 1) * sizeof(double2);
+    if ((e = cudaMalloc(&p.d_phase, bytes)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d_phi0, p.nrings * sizeof(double))) != cudaSuccess) return e;
+    e = cudaMemcpy(d_phi0, p.phi0.data(), p.nrings * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        phase_table_kernel<<<152 * 8, 256>>>(d_phi0, p.nrings, p.mmax, p.d_phase);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_phi0);
+    return e;
+}
+
+// Items: ring slots whose two rings share a length become one item; others are singles.
+// Longest first.  Lengths get their radices, tables and (Bluestein) filters.
+cudaError_t build_fft_tables(Plan &p)
+{
+    std::vector<FftItem> items;
+    for (int s = 0; s < p.nslots; ++s) {
+        const int a = p.slotN[s], b = p.slotS[s];
+        if (a >= 0 && b >= 0 && p.nphi[a] == p.nphi[b]) {
+            items.push_back({a, b, -1, (int)p.nphi[a]});
+        } else {
+            if (a >= 0) items.push_back({a, -1, -1, (int)p.nphi[a]});
+            if (b >= 0) items.push_back({b, -1, -1, (int)p.nphi[b]});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const FftItem &x, const FftItem &y) { return x.n > y.n; });
+
+    std::map<int, int> len_id;
+    std::vector<TabJob> jobs;
+    std::vector<int> blue_ids;
+    int64_t off = 0;
+    int maxlen = 1;
+    p.lens.clear();
+    for (auto &it : items) {
+        auto f = len_id.find(it.n);
+        if (f != len_id.end()) {
+            it.len_id = f->second;
+            continue;
+        }
+        FftLen L{};
+        L.n = it.n;
+        std::vector<int> fac;
+        if (factor_smooth(it.n, fac)) {
+            L.M = 0;
+            L.tw = off;
+            jobs.push_back({off, it.n, 0});
+            off += it.n;
+            maxlen = std::max(maxlen, it.n);
+        } else {
+            int M = 1;
+            while (M < 2 * it.n - 1) M <<= 1;
+            factor_smooth(M, fac);
+            L.M = M;
+            L.tw = off;
+            jobs.push_back({off, M, 0});
+            off += M;
+            L.chirp = off;
+            jobs.push_back({off, it.n, 1});
+            off += it.n;
+            L.filt = off;
+            off += M;
+            maxlen = std::max(maxlen, M);
+            blue_ids.push_back((int)p.lens.size());
+        }
+        if ((int)fac.size() > 24) return cudaErrorInvalidValue;
+        L.nfac = (int)fac.size();
+        for (size_t i = 0; i < fac.size(); ++i) L.fac[i] = fac[i];
+        it.len_id = (int)p.lens.size();
+        len_id[it.n] = it.len_id;
+        p.lens.push_back(L);
+    }
+    p.nitems = (int)items.size();
+    p.nlens = (int)p.lens.size();
+    p.fft_maxlen = maxlen;
+    p.fft_tab_len = off;
+
+    cudaError_t e;
+    TabJob *d_jobs = nullptr;
+    int *d_blue = nullptr;
+    double2 *d_scr = nullptr;
+    if ((e = cudaMalloc(&p.d_items, sizeof(FftItem) * items.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p.d_lens, sizeof(FftLen) * p.lens.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p.d_fft_tab, sizeof(double2) * std::max<int64_t>(off, 1))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(p.d_items, items.data(), sizeof(FftItem) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(p.d_lens, p.lens.data(), sizeof(FftLen) * p.lens.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&d_jobs, sizeof(TabJob) * jobs.size())) != cudaSuccess) return e;
+    e = cudaMemcpy(d_jobs, jobs.data(), sizeof(TabJob) * jobs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        fill_tables_kernel<<<(unsigned)std::min<size_t>(jobs.size(), 152 * 8), 256>>>(d_jobs, (int)jobs.size(),
+                                                                                   p.d_fft_tab);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !blue_ids.empty()) {
+        const int g = (int)std::min<size_t>(blue_ids.size(), 152);
+        e = cudaMalloc(&d_blue, sizeof(int) * blue_ids.size());
+        if (e == cudaSuccess) e = cudaMemcpy(d_blue, blue_ids.data(), sizeof(int) * blue_ids.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)g * 3 * maxlen * sizeof(double2));
+        if (e == cudaSuccess) {
+            bluestein_filter_kernel<<<g, FFT_T>>>(p.d_lens, d_blue, (int)blue_ids.size(), p.d_fft_tab, d_scr, maxlen);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_jobs);
+    cudaFree(d_blue);
+    cudaFree(d_scr);
+    return e;
+}
+
+}  // namespace sht

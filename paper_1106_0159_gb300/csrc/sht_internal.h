@@ -1,0 +1,92 @@
+// Internal plan layout shared by the host plan code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sht.h"
+
+namespace sht {
+
+// One complex FFT of length n on the ring stage: ring ringA rides on the real
+// part and ringB (or -1) on the imaginary part (two real rings per complex
+// transform).
+struct FftItem {
+    int ringA;
+    int ringB;
+    int len_id;   // index into the length table
+    int n;
+};
+
+// Everything a CTA needs to run a length-n DFT with the + sign,
+// y_k = sum_j x_j exp(+2 pi i j k / n).  Smooth n runs as Stockham passes
+// with the radices fac[]; otherwise Bluestein with a power-of-two M.
+struct FftLen {
+    int n;
+    int M;            // Bluestein convolution length, 0 when n is smooth
+    int nfac;         // radices of n (smooth) or of M (Bluestein)
+    int fac[24];
+    int64_t tw;       // offset of exp(2 pi i k / n), k < n   (smooth) or of exp(2 pi i k / M), k < M (Bluestein)
+    int64_t chirp;    // offset of exp(i pi j^2 / n), j < n   (Bluestein)
+    int64_t filt;     // offset of FFT_M(h) / M, M entries      (Bluestein)
+};
+
+struct Plan {
+    int lmax = 0, mmax = 0, nrings = 0;
+    int64_t npix = 0, nalm = 0;
+    int grid = 0;
+    std::vector<int64_t> nphi, ofs;
+    std::vector<double> theta, phi0, w;
+
+    // ring slots after north/south pairing, ordered by colatitude of the north member
+    int nslots = 0;
+    std::vector<int> slotN, slotS;     // ring index or -1
+    std::vector<double> slotTheta;     // colatitude used for lambda (northern hemisphere)
+
+    // device tables
+    int *d_slotN = nullptr, *d_slotS = nullptr;
+    double *d_u = nullptr;      // 1 - cos(theta) per slot
+    double *d_s = nullptr;      // sin(theta) per slot
+    double *d_alpha = nullptr;  // [nalm] recurrence coefficients (see legendre.cu)
+    double *d_cfac = nullptr;   // [nalm] lambda_lm = cfac * y_lm
+    int64_t *d_ofs = nullptr;   // [nrings + 1]
+    int *d_nphi = nullptr;      // [nrings]
+    double *d_w = nullptr;      // [nrings]
+    double2 *d_phase = nullptr; // [nrings][mmax + 1] exp(i m phi0_r)
+
+    int nitems = 0;
+    FftItem *d_items = nullptr;
+    int nlens = 0;
+    FftLen *d_lens = nullptr;
+    std::vector<FftLen> lens;
+    double2 *d_fft_tab = nullptr;
+    int64_t fft_tab_len = 0;
+    int fft_maxlen = 0;         // per-CTA scratch length (complex entries, per buffer)
+
+    // workspace, grown on demand
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+
+    std::string last_error;
+};
+
+// launch helpers (legendre.cu, ringfft.cu); return cudaGetLastError()
+cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st);
+cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
+                                 cudaStream_t st);
+size_t legendre_anal_partial_bytes(const Plan &p, int nmaps);
+cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
+                              cudaStream_t st);
+cudaError_t launch_ring_anal(const Plan &p, const double *map, double2 *delta, double2 *scratch, int nmaps,
+                             cudaStream_t st);
+size_t ring_scratch_bytes(const Plan &p);
+int ring_grid(const Plan &p);
+
+// plan-time table builders (ringfft.cu); synchronous on the legacy stream
+cudaError_t build_phase_table(Plan &p);
+cudaError_t build_fft_tables(Plan &p);
+
+}  // namespace sht

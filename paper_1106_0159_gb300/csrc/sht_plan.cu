@@ -1,0 +1,486 @@
+// Host side of the library: argument checks, plan construction (ring
+// pairing, recurrence tables, ring-stage tables), workspace, and the C ABI
+// entry points declared in include/sht.h.
+#include "sht_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+using sht::Plan;
+
+struct sht_plan_s {
+    Plan p;
+};
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+sht_status cuda_fail(Plan &p, cudaError_t e, const char *where)
+{
+    p.last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? SHT_ENOMEM : SHT_ECUDA;
+}
+
+void free_plan_device(Plan &p)
+{
+    void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac, p.d_ofs,
+                    p.d_nphi,  p.d_w,     p.d_phase, p.d_items, p.d_lens,    p.d_fft_tab, p.d_ws};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    p.d_slotN = p.d_slotS = nullptr;
+    p.d_u = p.d_s = p.d_alpha = p.d_cfac = p.d_w = nullptr;
+    p.d_ofs = nullptr;
+    p.d_nphi = nullptr;
+    p.d_phase = nullptr;
+    p.d_items = nullptr;
+    p.d_lens = nullptr;
+    p.d_fft_tab = nullptr;
+    p.d_ws = nullptr;
+    p.ws_bytes = 0;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const T *src, size_t n)
+{
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(n, 1));
+    if (e != cudaSuccess) return e;
+    if (n) e = cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+    return e;
+}
+
+// North/south pairing: rings whose colatitudes add to pi (within a few ulp of
+// pi) share one lambda recurrence.  Every slot is evaluated at the northern
+// colatitude of the pair.
+void pair_rings(Plan &p)
+{
+    const double tol = 4e-15;
+    std::vector<int> idx(p.nrings);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return p.theta[a] < p.theta[b]; });
+    struct Slot {
+        int n, s;
+        double th;
+    };
+    std::vector<Slot> slots;
+    auto single = [&](int r) {
+        if (p.theta[r] <= 0.5 * PI)
+            slots.push_back({r, -1, p.theta[r]});
+        else
+            slots.push_back({-1, r, PI - p.theta[r]});
+    };
+    int i = 0, j = p.nrings - 1;
+    while (i <= j) {
+        if (i == j) {
+            single(idx[i]);
+            break;
+        }
+        const int a = idx[i], b = idx[j];
+        const double sum = p.theta[a] + p.theta[b];
+        if (std::fabs(sum - PI) <= tol) {
+            slots.push_back({a, b, p.theta[a]});
+            ++i;
+            --j;
+        } else if (sum < PI) {
+            single(a);
+            ++i;
+        } else {
+            single(b);
+            --j;
+        }
+    }
+    std::stable_sort(slots.begin(), slots.end(), [](const Slot &x, const Slot &y) { return x.th < y.th; });
+    p.nslots = (int)slots.size();
+    p.slotN.resize(slots.size());
+    p.slotS.resize(slots.size());
+    p.slotTheta.resize(slots.size());
+    for (size_t k = 0; k < slots.size(); ++k) {
+        p.slotN[k] = slots[k].n;
+        p.slotS[k] = slots[k].s;
+        p.slotTheta[k] = slots[k].th;
+    }
+}
+
+// Recurrence tables in the normalised variable y_l = lambda_l / c_l (see legendre.cu):
+// alpha[index(m,m)] = mu_m, alpha[index(m+1,m)] = sqrt(2m+3) (eq. pm1m),
+// alpha[index(l,m)] = beta_l c_{l-1} / c_l for l >= m+2 (eqs. assLegRec, betaDef),
+// cfac[index(l,m)] = c_l with c_m = c_{m+1} = 1, c_l = (beta_l / beta_{l-1}) c_{l-2}.
+void recurrence_tables(int lmax, int mmax, std::vector<double> &alpha, std::vector<double> &cfac)
+{
+    const int64_t nalm = sht_nalm(lmax, mmax);
+    alpha.assign(nalm, 0.0);
+    cfac.assign(nalm, 0.0);
+    long double mu2 = 1.0L / (4.0L * 3.14159265358979323846264338327950288L);  // mu_0^2
+    for (int m = 0; m <= mmax; ++m) {
+        if (m > 0) mu2 *= (long double)(2 * m + 1) / (long double)(2 * m);  // eq. (pmm)
+        const int64_t base = sht_alm_index(lmax, m, m);
+        alpha[base] = (double)std::sqrt(mu2);
+        cfac[base] = 1.0;
+        if (m + 1 > lmax) continue;
+        alpha[base + 1] = std::sqrt(2.0 * m + 3.0);
+        cfac[base + 1] = 1.0;
+        double c2 = 1.0, c1 = 1.0;            // c_{l-2}, c_{l-1}
+        double bprev = std::sqrt(2.0 * m + 3.0);  // beta_{m+1,m}
+        const double m2 = (double)m * m;
+        for (int l = m + 2; l <= lmax; ++l) {
+            const double L = (double)l;
+            const double b = std::sqrt((4.0 * L * L - 1.0) / (L * L - m2));
+            const double c = (b / bprev) * c2;
+            alpha[base + (l - m)] = b * c1 / c;
+            cfac[base + (l - m)] = c;
+            c2 = c1;
+            c1 = c;
+            bprev = b;
+        }
+    }
+}
+
+sht_status ensure_workspace(Plan &p, size_t need)
+{
+    if (p.ws_bytes >= need) return SHT_OK;
+    if (p.d_ws) {
+        cudaError_t e = cudaFree(p.d_ws);
+        p.d_ws = nullptr;
+        p.ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(p, e, "workspace free");
+    }
+    cudaError_t e = cudaMalloc(&p.d_ws, need);
+    if (e != cudaSuccess) {
+        p.d_ws = nullptr;
+        cudaGetLastError();
+        return cuda_fail(p, e, "workspace allocation");
+    }
+    p.ws_bytes = need;
+    return SHT_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t delta_bytes(const Plan &p, int nmaps) { return (size_t)nmaps * p.nrings * (p.mmax + 1) * sizeof(double2); }
+
+sht_status check_call(sht_plan_t plan, const void *in, const void *out, int nmaps)
+{
+    if (!plan) return SHT_EINVAL;
+    if (nmaps < 0) return SHT_EINVAL;
+    if (nmaps > 0 && (!in || !out)) return SHT_EINVAL;
+    if (nmaps > 0 && in == out) return SHT_EINVAL;
+    return SHT_OK;
+}
+
+sht_status after_launch(Plan &p, cudaError_t e, const char *where)
+{
+    if (e != cudaSuccess) return cuda_fail(p, e, where);
+    return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t sht_nalm(int lmax, int mmax)
+{
+    if (lmax < 0 || mmax < 0 || mmax > lmax) return -1;
+    return (int64_t)(mmax + 1) * (lmax + 1) - (int64_t)mmax * (mmax + 1) / 2;
+}
+
+int64_t sht_alm_index(int lmax, int l, int m)
+{
+    if (lmax < 0 || m < 0 || l < m || l > lmax) return -1;
+    return (int64_t)m * (2 * (int64_t)lmax + 3 - m) / 2 + (l - m);
+}
+
+const char *sht_status_string(sht_status s)
+{
+    switch (s) {
+    case SHT_OK: return "ok";
+    case SHT_EINVAL: return "invalid argument";
+    case SHT_ENOMEM: return "out of memory";
+    case SHT_ECUDA: return "CUDA error";
+    case SHT_EUNSUPPORTED: return "unsupported";
+    case SHT_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *sht_plan_last_error(sht_plan_t plan) { return plan ? plan->p.last_error.c_str() : ""; }
+
+int64_t sht_plan_npix(sht_plan_t plan) { return plan ? plan->p.npix : -1; }
+int sht_plan_nrings(sht_plan_t plan) { return plan ? plan->p.nrings : -1; }
+int sht_plan_npairs(sht_plan_t plan) { return plan ? plan->p.nslots : -1; }
+
+size_t sht_workspace_bytes(sht_plan_t plan, int nmaps)
+{
+    if (!plan || nmaps <= 0) return 0;
+    const Plan &p = plan->p;
+    const size_t d = align256(delta_bytes(p, nmaps));
+    const size_t r = align256(sht::ring_scratch_bytes(p));
+    const size_t a = align256(sht::legendre_anal_partial_bytes(p, nmaps));
+    return d + std::max(r, a);
+}
+
+sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int64_t *nphi, const double *theta,
+                           const double *phi0, const double *w, int lmax, int mmax)
+{
+    if (!out) return SHT_EINVAL;
+    *out = nullptr;
+    if (nrings < 1 || !nphi || !theta || !phi0 || !w) return SHT_EINVAL;
+    if (lmax < 0 || mmax < 0 || mmax > lmax || lmax > 16383) return SHT_EINVAL;
+    if ((int)grid < 0 || (int)grid > 2) return SHT_EINVAL;
+    for (int r = 0; r < nrings; ++r) {
+        if (nphi[r] < 1 || nphi[r] > (1 << 20)) return SHT_EINVAL;
+        if (!is_finite(theta[r]) || theta[r] < 0.0 || theta[r] > PI) return SHT_EINVAL;
+        if (!is_finite(phi0[r]) || !is_finite(w[r])) return SHT_EINVAL;
+        if (std::fabs(phi0[r]) > 1e3) return SHT_EINVAL;
+    }
+    sht_plan_s *h = new (std::nothrow) sht_plan_s();
+    if (!h) return SHT_ENOMEM;
+    Plan &p = h->p;
+    p.lmax = lmax;
+    p.mmax = mmax;
+    p.nrings = nrings;
+    p.grid = (int)grid;
+    p.nalm = sht_nalm(lmax, mmax);
+    p.nphi.assign(nphi, nphi + nrings);
+    p.theta.assign(theta, theta + nrings);
+    p.phi0.assign(phi0, phi0 + nrings);
+    p.w.assign(w, w + nrings);
+    p.ofs.resize(nrings + 1);
+    p.ofs[0] = 0;
+    for (int r = 0; r < nrings; ++r) p.ofs[r + 1] = p.ofs[r] + nphi[r];
+    p.npix = p.ofs[nrings];
+
+    pair_rings(p);
+    std::vector<double> u(p.nslots), s(p.nslots);
+    for (int k = 0; k < p.nslots; ++k) {
+        const double th = p.slotTheta[k];
+        const double h2 = std::sin(0.5 * th);
+        u[k] = 2.0 * h2 * h2;  // 1 - cos(theta), accurate near the pole
+        s[k] = std::sin(th);
+    }
+    std::vector<double> alpha, cfac;
+    recurrence_tables(lmax, mmax, alpha, cfac);
+    std::vector<int> nphi32(nrings);
+    for (int r = 0; r < nrings; ++r) nphi32[r] = (int)nphi[r];
+
+    cudaError_t e = cudaSuccess;
+    const char *where = "plan upload";
+    if (e == cudaSuccess) e = upload(&p.d_slotN, p.slotN.data(), p.slotN.size());
+    if (e == cudaSuccess) e = upload(&p.d_slotS, p.slotS.data(), p.slotS.size());
+    if (e == cudaSuccess) e = upload(&p.d_u, u.data(), u.size());
+    if (e == cudaSuccess) e = upload(&p.d_s, s.data(), s.size());
+    if (e == cudaSuccess) e = upload(&p.d_alpha, alpha.data(), alpha.size());
+    if (e == cudaSuccess) e = upload(&p.d_cfac, cfac.data(), cfac.size());
+    if (e == cudaSuccess) e = upload(&p.d_ofs, p.ofs.data(), p.ofs.size());
+    if (e == cudaSuccess) e = upload(&p.d_nphi, nphi32.data(), nphi32.size());
+    if (e == cudaSuccess) e = upload(&p.d_w, p.w.data(), p.w.size());
+    if (e == cudaSuccess) {
+        where = "phase table";
+        e = sht::build_phase_table(p);
+    }
+    if (e == cudaSuccess) {
+        where = "ring tables";
+        e = sht::build_fft_tables(p);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sht_status st = (e == cudaErrorMemoryAllocation) ? SHT_ENOMEM : SHT_ECUDA;
+        if (e == cudaErrorInvalidValue && std::string(where) == "ring tables") st = SHT_EUNSUPPORTED;
+        free_plan_device(p);
+        delete h;
+        (void)where;
+        return st;
+    }
+    *out = h;
+    return SHT_OK;
+}
+
+void sht_plan_destroy(sht_plan_t plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan_device(plan->p);
+    delete plan;
+}
+
+sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, alm, delta, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    return after_launch(p,
+                        sht::launch_legendre_synth(p, (const double2 *)alm, (double2 *)delta, nmaps,
+                                                   (cudaStream_t)stream),
+                        "legendre_synth");
+}
+
+sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, delta, map, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    st = ensure_workspace(p, align256(sht::ring_scratch_bytes(p)));
+    if (st != SHT_OK) return st;
+    return after_launch(p,
+                        sht::launch_ring_synth(p, (const double2 *)delta, map, (double2 *)p.d_ws, nmaps,
+                                               (cudaStream_t)stream),
+                        "ring_synth");
+}
+
+sht_status sht_ring_anal(sht_plan_t plan, const double *map, void *delta, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, map, delta, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    st = ensure_workspace(p, align256(sht::ring_scratch_bytes(p)));
+    if (st != SHT_OK) return st;
+    return after_launch(p,
+                        sht::launch_ring_anal(p, map, (double2 *)delta, (double2 *)p.d_ws, nmaps,
+                                              (cudaStream_t)stream),
+                        "ring_anal");
+}
+
+sht_status sht_legendre_anal(sht_plan_t plan, const void *delta, void *alm, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, delta, alm, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    st = ensure_workspace(p, align256(sht::legendre_anal_partial_bytes(p, nmaps)));
+    if (st != SHT_OK) return st;
+    return after_launch(p,
+                        sht::launch_legendre_anal(p, (const double2 *)delta, (double2 *)alm, (double2 *)p.d_ws,
+                                                  nmaps, (cudaStream_t)stream),
+                        "legendre_anal");
+}
+
+sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, alm, map, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    const size_t d = align256(delta_bytes(p, nmaps));
+    st = ensure_workspace(p, d + align256(sht::ring_scratch_bytes(p)));
+    if (st != SHT_OK) return st;
+    double2 *delta = (double2 *)p.d_ws;
+    double2 *scratch = (double2 *)((char *)p.d_ws + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = sht::launch_legendre_synth(p, (const double2 *)alm, delta, nmaps, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "legendre_synth");
+    return after_launch(p, sht::launch_ring_synth(p, delta, map, scratch, nmaps, s), "ring_synth");
+}
+
+sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, map, alm, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    const size_t d = align256(delta_bytes(p, nmaps));
+    const size_t r = align256(sht::ring_scratch_bytes(p));
+    const size_t a = align256(sht::legendre_anal_partial_bytes(p, nmaps));
+    st = ensure_workspace(p, d + std::max(r, a));
+    if (st != SHT_OK) return st;
+    double2 *delta = (double2 *)p.d_ws;
+    double2 *scratch = (double2 *)((char *)p.d_ws + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = sht::launch_ring_anal(p, map, delta, scratch, nmaps, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "ring_anal");
+    return after_launch(p, sht::launch_legendre_anal(p, delta, (double2 *)alm, scratch, nmaps, s), "legendre_anal");
+}
+
+// ------------------------------------------------------------------ grids
+
+sht_status sht_geom_healpix(int nside, int64_t *nphi, double *theta, double *phi0, double *w)
+{
+    if (nside < 1 || nside > (1 << 13) || !nphi || !theta || !phi0 || !w) return SHT_EINVAL;
+    const int nr = 4 * nside - 1;
+    const double npix = 12.0 * nside * (double)nside;
+    for (int k = 0; k < nr; ++k) {
+        const int i = k + 1;
+        const int north = (i <= 2 * nside) ? i : 4 * nside - i;
+        double th, p0;
+        int64_t n;
+        if (north < nside) {
+            n = 4 * north;
+            th = 2.0 * std::asin(north / (std::sqrt(6.0) * nside));
+            p0 = PI / (4.0 * north);
+        } else {
+            n = 4 * (int64_t)nside;
+            const double z = 4.0 / 3.0 - 2.0 * north / (3.0 * nside);
+            th = std::acos(z);
+            p0 = ((i - nside) % 2 == 0) ? PI / (4.0 * nside) : 0.0;
+        }
+        if (i > 2 * nside) th = PI - th;
+        nphi[k] = n;
+        theta[k] = th;
+        phi0[k] = p0;
+        w[k] = 4.0 * PI / npix;
+    }
+    return SHT_OK;
+}
+
+// Gauss-Legendre nodes by Newton's method on P_N from the asymptotic guess,
+// weights 2 / ((1 - x^2) P_N'(x)^2); the southern half mirrors the northern one.
+sht_status sht_geom_gauss_legendre(int nrings, int64_t nphi, int64_t *nphi_out, double *theta, double *phi0, double *w)
+{
+    if (nrings < 1 || nrings > (1 << 16) || nphi < 1 || nphi > (1 << 20) || !nphi_out || !theta || !phi0 || !w)
+        return SHT_EINVAL;
+    const int N = nrings;
+    for (int j = 0; j < (N + 1) / 2; ++j) {
+        double x = std::cos(PI * (j + 0.75) / (N + 0.5));
+        double dp = 1.0;
+        int converged = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int l = 2; l <= N; ++l) {
+                const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (N == 1) {
+                p1 = x;
+                p0 = 1.0;
+            }
+            dp = N * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-15) {
+                if (++converged >= 2) break;
+            }
+        }
+        // final derivative at the converged node
+        {
+            double p0 = 1.0, p1 = x;
+            for (int l = 2; l <= N; ++l) {
+                const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (N == 1) {
+                p1 = x;
+                p0 = 1.0;
+            }
+            dp = N * (x * p1 - p0) / (x * x - 1.0);
+        }
+        const double wg = 2.0 / ((1.0 - x * x) * dp * dp);
+        const int js = N - 1 - j;
+        if (js == j) x = 0.0;
+        const double th = std::acos(x);
+        theta[j] = th;
+        w[j] = 2.0 * PI * wg / (double)nphi;
+        if (js != j) {
+            theta[js] = PI - th;
+            w[js] = w[j];
+        }
+    }
+    for (int r = 0; r < N; ++r) {
+        nphi_out[r] = nphi;
+        phi0[r] = 0.0;
+    }
+    return SHT_OK;
+}
+
+}  // extern "C"

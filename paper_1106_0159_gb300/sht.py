@@ -1,0 +1,262 @@
+"""Python binding of the C ABI in ``include/sht.h`` (argument marshalling only).
+
+Every transform step runs in the CUDA library ``_lib/libsht.so``; this module
+only checks tensor shapes, passes device pointers and the current CUDA
+stream, and turns status codes into exceptions.  There is no CPU path: if
+the library cannot be loaded the calls raise.
+
+PyTorch supplies device memory and streams.  Coefficients are complex128
+tensors of shape [nmaps, nalm] in m-major triangular order, maps float64
+tensors of shape [nmaps, npix], Delta intermediates complex128
+[nmaps, nrings, mmax + 1].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libsht.so")
+_lock = threading.Lock()
+_lib = None
+
+SHT_OK, SHT_EINVAL, SHT_ENOMEM, SHT_ECUDA, SHT_EUNSUPPORTED, SHT_ETIMEOUT = range(6)
+GRID_CUSTOM, GRID_HEALPIX, GRID_GAUSS_LEGENDRE = 0, 1, 2
+
+# every entry point the header declares (the test suite checks the library exports them)
+EXPORTS = (
+    "sht_plan_create", "sht_plan_destroy", "sht_alm2map", "sht_map2alm",
+    "sht_legendre_synth", "sht_ring_synth", "sht_ring_anal", "sht_legendre_anal",
+    "sht_nalm", "sht_alm_index", "sht_plan_npix", "sht_plan_nrings", "sht_plan_npairs",
+    "sht_workspace_bytes", "sht_geom_healpix", "sht_geom_gauss_legendre",
+    "sht_status_string", "sht_plan_last_error",
+)
+
+
+class ShtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load (building first if absent or stale) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import _build
+        _build.build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        S = ctypes.c_size_t
+        sig = {
+            "sht_plan_create": (I, [ctypes.POINTER(P), I, I, P, P, P, P, I, I]),
+            "sht_plan_destroy": (None, [P]),
+            "sht_alm2map": (I, [P, P, P, I, P]),
+            "sht_map2alm": (I, [P, P, P, I, P]),
+            "sht_legendre_synth": (I, [P, P, P, I, P]),
+            "sht_ring_synth": (I, [P, P, P, I, P]),
+            "sht_ring_anal": (I, [P, P, P, I, P]),
+            "sht_legendre_anal": (I, [P, P, P, I, P]),
+            "sht_nalm": (I64, [I, I]),
+            "sht_alm_index": (I64, [I, I, I]),
+            "sht_plan_npix": (I64, [P]),
+            "sht_plan_nrings": (I, [P]),
+            "sht_plan_npairs": (I, [P]),
+            "sht_workspace_bytes": (S, [P, I]),
+            "sht_geom_healpix": (I, [I, P, P, P, P]),
+            "sht_geom_gauss_legendre": (I, [I, I64, P, P, P, P]),
+            "sht_status_string": (ctypes.c_char_p, [I]),
+            "sht_plan_last_error": (ctypes.c_char_p, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, plan_ptr=None, what: str = ""):
+    if status == SHT_OK:
+        return
+    lib = load()
+    msg = lib.sht_status_string(status).decode()
+    if plan_ptr:
+        extra = lib.sht_plan_last_error(plan_ptr).decode()
+        if extra:
+            msg += ": " + extra
+    if what:
+        msg = what + ": " + msg
+    if status == SHT_EINVAL:
+        raise ValueError(msg)
+    raise ShtError(status, msg)
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def nalm(lmax: int, mmax: int) -> int:
+    return int(load().sht_nalm(int(lmax), int(mmax)))
+
+
+def alm_index(lmax: int, l: int, m: int) -> int:
+    return int(load().sht_alm_index(int(lmax), int(l), int(m)))
+
+
+def healpix_geometry(nside: int):
+    """(nphi, theta, phi0, w) of the HEALPix grid, from the library's host helper."""
+    nr = 4 * int(nside) - 1
+    if nr < 3:
+        raise ValueError("nside must be >= 1")
+    nphi = np.zeros(nr, np.int64)
+    th, p0, w = (np.zeros(nr) for _ in range(3))
+    _check(load().sht_geom_healpix(int(nside), _np_ptr(nphi), _np_ptr(th), _np_ptr(p0), _np_ptr(w)), what="healpix")
+    return nphi, th, p0, w
+
+
+def gauss_legendre_geometry(nrings: int, nphi: int):
+    """(nphi, theta, phi0, w) of a Gauss-Legendre grid, from the library's host helper."""
+    if int(nrings) < 1:
+        raise ValueError("nrings must be >= 1")
+    n = np.zeros(int(nrings), np.int64)
+    th, p0, w = (np.zeros(int(nrings)) for _ in range(3))
+    _check(load().sht_geom_gauss_legendre(int(nrings), int(nphi), _np_ptr(n), _np_ptr(th), _np_ptr(p0), _np_ptr(w)),
+           what="gauss_legendre")
+    return n, th, p0, w
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A transform plan: ring geometry and band limits, with device tables.
+
+    ``geom`` is (nphi, theta, phi0, w) per ring (host arrays, copied).
+    """
+
+    def __init__(self, geom, lmax: int, mmax: int | None = None, grid: int = GRID_CUSTOM):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the spherical harmonic transforms need a CUDA device")
+        torch.cuda.init()
+        lib = load()
+        mmax = int(lmax) if mmax is None else int(mmax)
+        nphi, theta, phi0, w = geom
+        self._nphi = np.ascontiguousarray(nphi, dtype=np.int64)
+        self._theta = np.ascontiguousarray(theta, dtype=np.float64)
+        self._phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        self._w = np.ascontiguousarray(w, dtype=np.float64)
+        n = len(self._nphi)
+        if not (len(self._theta) == len(self._phi0) == len(self._w) == n):
+            raise ValueError("geometry arrays differ in length")
+        h = ctypes.c_void_p()
+        st = lib.sht_plan_create(ctypes.byref(h), int(grid), n, _np_ptr(self._nphi), _np_ptr(self._theta),
+                                 _np_ptr(self._phi0), _np_ptr(self._w), int(lmax), mmax)
+        _check(st, what="sht_plan_create")
+        self._h = h
+        self.lmax, self.mmax = int(lmax), mmax
+        self.nrings = n
+        self.npix = int(lib.sht_plan_npix(h))
+        self.nalm = nalm(lmax, mmax)
+        self.npairs = int(lib.sht_plan_npairs(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sht_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, nmaps: int) -> int:
+        return int(load().sht_workspace_bytes(self._h, int(nmaps)))
+
+    # -- tensor checks ------------------------------------------------------
+    def _dev(self, t, dtype, tail, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        if t.dim() == len(tail):
+            t = t.unsqueeze(0)
+        if tuple(t.shape[1:]) != tuple(tail):
+            raise ValueError("%s has shape %s, expected [nmaps, %s]" % (name, tuple(t.shape), tail))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return t
+
+    def _out(self, out, shape, dtype, like):
+        import torch
+        if out is None:
+            return torch.empty(shape, dtype=dtype, device=like.device)
+        o = self._dev(out, dtype, shape[1:], "out")
+        if o.shape[0] != shape[0]:
+            raise ValueError("out has %d maps, expected %d" % (o.shape[0], shape[0]))
+        return o
+
+    def _run(self, fn, src, dst, nmaps, stream):
+        st = fn(self._h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), int(nmaps),
+                _stream_ptr(stream))
+        _check(st, self._h, fn.__name__)
+
+    # -- transforms ---------------------------------------------------------
+    def alm2map(self, alm, out=None, stream=None):
+        """Synthesis (Algorithm 2): [nmaps, nalm] complex128 -> [nmaps, npix] float64."""
+        import torch
+        a = self._dev(alm, torch.complex128, (self.nalm,), "alm")
+        o = self._out(out, (a.shape[0], self.npix), torch.float64, a)
+        self._run(load().sht_alm2map, a, o, a.shape[0], stream)
+        return o
+
+    def map2alm(self, m, out=None, stream=None):
+        """Analysis (Algorithm 1): [nmaps, npix] float64 -> [nmaps, nalm] complex128."""
+        import torch
+        s = self._dev(m, torch.float64, (self.npix,), "map")
+        o = self._out(out, (s.shape[0], self.nalm), torch.complex128, s)
+        self._run(load().sht_map2alm, s, o, s.shape[0], stream)
+        return o
+
+    def legendre_synth(self, alm, out=None, stream=None):
+        import torch
+        a = self._dev(alm, torch.complex128, (self.nalm,), "alm")
+        o = self._out(out, (a.shape[0], self.nrings, self.mmax + 1), torch.complex128, a)
+        self._run(load().sht_legendre_synth, a, o, a.shape[0], stream)
+        return o
+
+    def ring_synth(self, delta, out=None, stream=None):
+        import torch
+        d = self._dev(delta, torch.complex128, (self.nrings, self.mmax + 1), "delta")
+        o = self._out(out, (d.shape[0], self.npix), torch.float64, d)
+        self._run(load().sht_ring_synth, d, o, d.shape[0], stream)
+        return o
+
+    def ring_anal(self, m, out=None, stream=None):
+        import torch
+        s = self._dev(m, torch.float64, (self.npix,), "map")
+        o = self._out(out, (s.shape[0], self.nrings, self.mmax + 1), torch.complex128, s)
+        self._run(load().sht_ring_anal, s, o, s.shape[0], stream)
+        return o
+
+    def legendre_anal(self, delta, out=None, stream=None):
+        import torch
+        d = self._dev(delta, torch.complex128, (self.nrings, self.mmax + 1), "delta")
+        o = self._out(out, (d.shape[0], self.nalm), torch.complex128, d)
+        self._run(load().sht_legendre_anal, d, o, d.shape[0], stream)
+        return o

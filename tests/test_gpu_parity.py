@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Tolerance (the stated FP64 bar): max |x_gpu - x_oracle| / RMS(x_oracle) <= 1e-11
+over every output value of a call, for maps and for a_lm; Gauss-Legendre
+round trips <= 1e-12 of the RMS.  Small cases compare every output against
+the pixel-by-pixel oracle; the full-size cases compare sampled rings and
+sampled m against the separable oracle, plus properties that hold at any
+size (adjoint identity, determinism).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import geometry
+from paper_1106_0159_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+TOL_RT = 1e-12
+
+
+def _sht():
+    from paper_1106_0159_gb300 import sht
+    return sht
+
+
+def rel(x, ref):
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    return float(np.max(np.abs(x - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2)))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def plan_for(geom, lmax, mmax=None):
+    return _sht().Plan(geom, lmax, mmax)
+
+
+def test_library_is_the_in_tree_build():
+    sht = _sht()
+    lib = sht.load()
+    import os
+    assert os.path.abspath(lib._name) == os.path.abspath(sht.library_path())
+
+
+# ---------------------------------------------------------------- config 1: HEALPix Nside=32, lmax=mmax=64
+
+@pytest.fixture(scope="module")
+def c1():
+    geom = geometry.healpix(32)
+    return geom, plan_for(geom, 64)
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "uniform"])
+def test_c1_alm2map_against_pixel_oracle(c1, kind):
+    geom, p = c1
+    gen = inputs.gaussian_alm if kind == "gaussian" else inputs.uniform_alm
+    a = gen(64, 64, seed=11)
+    s = host(p.alm2map(dev(a)))[0]
+    ref = oracle.alm2map_exact(geom, a[0], 64, 64)
+    assert rel(s, ref) < TOL
+
+
+def test_c1_map2alm_against_pixel_oracle(c1):
+    geom, p = c1
+    s = inputs.white_map(geometry.npix(geom), seed=12)
+    a = host(p.map2alm(dev(s)))[0]
+    ref = oracle.map2alm_exact(geom, s[0], 64, 64)
+    assert rel(a, ref) < TOL
+    l, m = inputs.lm_arrays(64, 64)
+    assert np.all(a[m == 0].imag == 0)
+
+
+def test_c1_round_trip_matches_oracle_round_trip(c1):
+    geom, p = c1
+    a = inputs.gaussian_alm(64, 64, seed=13)
+    b = host(p.map2alm(p.alm2map(dev(a))))[0]
+    ref = oracle.map2alm_rings(geom, oracle.alm2map_rings(geom, a[0], 64, 64), 64, 64)
+    assert rel(b, ref) < TOL
+
+
+def test_c1_stage_legendre_synth(c1):
+    geom, p = c1
+    a = inputs.gaussian_alm(64, 64, seed=14)
+    d = host(p.legendre_synth(dev(a)))[0]
+    ref = oracle.delta_synth(geom, a[0], 64, 64)
+    assert rel(d, ref) < TOL
+
+
+def test_c1_stage_legendre_anal(c1):
+    geom, p = c1
+    d = inputs.random_delta(len(geom[0]), 64, seed=15)
+    a = host(p.legendre_anal(dev(d)))[0]
+    ms = np.arange(65)
+    ref = np.concatenate(oracle.legendre_anal(geom, d[0].T.copy(), 64, ms))
+    assert rel(a, ref) < TOL
+
+
+# ---------------------------------------------------------------- ring stage on awkward lengths
+
+def _awkward_geometry():
+    # lengths: 1, 2, 3, 4, 5, 7, 11, 13 (radix passes), 17, 97, 241 (Bluestein), 68 = 4*17,
+    # 4097 = 17 * 241, 1000, 128; unpaired rings and a mirrored pair of unequal length
+    nphi = np.array([1, 2, 3, 4, 5, 7, 11, 13, 17, 97, 241, 68, 4097, 1000, 128, 30, 31], np.int64)
+    rng = np.random.default_rng(5)
+    theta = np.sort(rng.uniform(0.05, math.pi - 0.05, len(nphi)))
+    theta[-1] = math.pi - theta[0]          # a pair with lengths 1 and 31
+    theta[-2] = math.pi - theta[3]          # a pair with lengths 4 and 30
+    phi0 = rng.uniform(0, 2 * math.pi, len(nphi))
+    w = rng.uniform(0.5, 2.0, len(nphi))
+    return nphi, theta, phi0, w
+
+
+@pytest.mark.parametrize("mmax", [0, 5, 40, 300])
+def test_ring_synth_awkward_lengths(mmax):
+    geom = _awkward_geometry()
+    p = plan_for(geom, mmax, mmax)
+    d = inputs.random_delta(len(geom[0]), mmax, seed=16, nmaps=2)
+    s = host(p.ring_synth(dev(d)))
+    for g in range(2):
+        ref = oracle.ring_synth(geom, d[g], mmax)
+        assert rel(s[g], ref) < TOL
+
+
+@pytest.mark.parametrize("mmax", [0, 5, 40, 300])
+def test_ring_anal_awkward_lengths(mmax):
+    geom = _awkward_geometry()
+    p = plan_for(geom, mmax, mmax)
+    s = inputs.white_map(geometry.npix(geom), seed=17, nmaps=2)
+    d = host(p.ring_anal(dev(s)))
+    for g in range(2):
+        ref = oracle.delta_anal(geom, s[g], np.arange(mmax + 1)).T
+        assert rel(d[g], ref) < TOL
+        assert np.all(d[g][:, 0].imag == 0)
+
+
+def test_gauss_legendre_grid_with_prime_lengths():
+    L = 130
+    geom = geometry.gauss_legendre(L + 1, 2 * L + 1)  # nphi = 261 = 9 * 29 -> Bluestein
+    p = plan_for(geom, L)
+    a = inputs.gaussian_alm(L, L, seed=18)
+    s = host(p.alm2map(dev(a)))[0]
+    rings = [0, 1, 40, 65, 100, L]
+    ref = oracle.alm2map_rings(geom, a[0], L, L, rings)
+    off = geometry.ring_offsets(geom)
+    got = np.concatenate([s[off[r]:off[r + 1]] for r in rings])
+    assert rel(got, ref) < TOL
+    b = host(p.map2alm(dev(s[None])))[0]
+    assert rel(b, a[0]) < TOL_RT
+
+
+# ---------------------------------------------------------------- multi-map, mmax < lmax, determinism, edges
+
+def test_multi_map_equals_single_map_calls():
+    geom = geometry.healpix(16)
+    L = 40
+    p = plan_for(geom, L)
+    a = inputs.gaussian_alm(L, L, seed=19, nmaps=7)
+    s_all = host(p.alm2map(dev(a)))
+    b_all = host(p.map2alm(dev(s_all)))
+    for g in (0, 3, 6):
+        s1 = host(p.alm2map(dev(a[g:g + 1])))[0]
+        assert np.array_equal(s1, s_all[g])
+        b1 = host(p.map2alm(dev(s_all[g:g + 1])))[0]
+        assert np.array_equal(b1, b_all[g])
+
+
+def test_mmax_below_lmax():
+    geom = geometry.healpix(8)
+    L, M = 24, 7
+    p = plan_for(geom, L, M)
+    a = inputs.uniform_alm(L, M, seed=20)
+    s = host(p.alm2map(dev(a)))[0]
+    assert rel(s, oracle.alm2map_exact(geom, a[0], L, M)) < TOL
+    b = host(p.map2alm(dev(s[None])))[0]
+    assert rel(b, oracle.map2alm_exact(geom, s, L, M)) < TOL
+
+
+def test_bitwise_deterministic():
+    geom = geometry.healpix(32)
+    p = plan_for(geom, 64)
+    a = dev(inputs.gaussian_alm(64, 64, seed=21, nmaps=2))
+    s1 = host(p.alm2map(a))
+    s2 = host(p.alm2map(a))
+    assert np.array_equal(s1, s2)
+    b1 = host(p.map2alm(dev(s1)))
+    b2 = host(p.map2alm(dev(s1)))
+    assert np.array_equal(b1, b2)
+
+
+def test_poles_single_ring_and_tiny_bands():
+    # rings at both poles and the equator, a one-pixel ring, lmax = 0 and mmax = 0
+    nphi = np.array([1, 3, 8, 5, 2], np.int64)
+    theta = np.array([0.0, 0.4, math.pi / 2, 2.0, math.pi])
+    phi0 = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    w = np.array([1.0, 0.5, 0.25, 0.5, 1.0])
+    geom = (nphi, theta, phi0, w)
+    for L, M in [(0, 0), (6, 0), (6, 6), (9, 4)]:
+        p = plan_for(geom, L, M)
+        a = inputs.uniform_alm(L, M, seed=22)
+        s = host(p.alm2map(dev(a)))[0]
+        assert rel(s, oracle.alm2map_exact(geom, a[0], L, M)) < TOL
+        b = host(p.map2alm(dev(s[None])))[0]
+        assert rel(b, oracle.map2alm_exact(geom, s, L, M)) < TOL
+    one = (np.array([7], np.int64), np.array([1.1]), np.array([0.0]), np.array([1.0]))
+    p = plan_for(one, 5)
+    a = inputs.gaussian_alm(5, 5, seed=23)
+    assert rel(host(p.alm2map(dev(a)))[0], oracle.alm2map_exact(one, a[0], 5, 5)) < TOL
+
+
+def test_zero_maps_and_bad_tensors():
+    geom = geometry.healpix(4)
+    p = plan_for(geom, 8)
+    a = torch.zeros((0, p.nalm), dtype=torch.complex128, device="cuda")
+    assert p.alm2map(a).shape == (0, p.npix)
+    with pytest.raises(TypeError):
+        p.alm2map(torch.zeros((1, p.nalm), dtype=torch.complex64, device="cuda"))
+    with pytest.raises(ValueError):
+        p.alm2map(torch.zeros((1, p.nalm + 1), dtype=torch.complex128, device="cuda"))
+    with pytest.raises(TypeError):
+        p.map2alm(torch.zeros((1, p.npix), dtype=torch.float64))
+
+
+# ---------------------------------------------------------------- full sizes (sampled) and any-size properties
+
+def _sample_rings(nside):
+    nr = 4 * nside - 1
+    return sorted({0, 1, 2, nside - 2, nside - 1, nside, 2 * nside - 1, 3 * nside - 1, 3 * nside,
+                   nr - 2, nr - 1, nr // 3})
+
+
+def _check_sampled(geom, p, L, a, s_gpu, rings):
+    ref = oracle.alm2map_rings(geom, a, L, L, rings)
+    off = geometry.ring_offsets(geom)
+    got = np.concatenate([s_gpu[off[r]:off[r + 1]] for r in rings])
+    return rel(got, ref)
+
+
+@pytest.mark.parametrize("nside,L", [(1024, 2048), (2048, 4096)])
+def test_full_size_healpix_sampled(nside, L):
+    geom = geometry.healpix(nside)
+    p = plan_for(geom, L)
+    a = inputs.gaussian_alm(L, L, seed=24)
+    s = host(p.alm2map(dev(a)))[0]
+    assert _check_sampled(geom, p, L, a[0], s, _sample_rings(nside)) < TOL
+    # analysis of a white-noise map on sampled m (all rings), against the separable oracle
+    wm = inputs.white_map(geometry.npix(geom), seed=25)
+    b = host(p.map2alm(dev(wm)))[0]
+    ms = [0, 1, 2, L // 4, L // 2 + 1, L - 1, L]
+    refs = oracle.map2alm_ms(geom, wm[0], L, ms)
+    got = np.concatenate([b[oracle.alm_index(L, m, m):oracle.alm_index(L, m, m) + L - m + 1] for m in ms])
+    assert rel(got, np.concatenate(refs)) < TOL
+    # adjoint identity over the whole sphere: sum_p w s alm2map(a) = <map2alm(s), a>
+    wpix = np.repeat(geom[3], geom[0])
+    lhs = float(np.sum(wpix * wm[0] * s))
+    l, m = inputs.lm_arrays(L, L)
+    rhs = float(np.sum(np.where(m == 0, 1.0, 2.0) * (b * np.conj(a[0])).real))
+    assert abs(lhs - rhs) < 1e-11 * math.sqrt(np.sum(np.abs(b) ** 2) * np.sum(np.abs(a[0]) ** 2))
+
+
+def test_gauss_legendre_round_trip_lmax2048():
+    L = 2048
+    geom = geometry.gauss_legendre(L + 1, 2 * L + 1)  # 2049 rings x 4097 = 17 * 241 pixels
+    p = plan_for(geom, L)
+    a = inputs.gaussian_alm(L, L, seed=26)
+    s = p.alm2map(dev(a))
+    b = host(p.map2alm(s))[0]
+    assert rel(b, a[0]) < TOL_RT
+    s = host(s)[0]
+    rings = [0, 1, 500, 1024, 2047, 2048]
+    assert _check_sampled(geom, p, L, a[0], s, rings) < TOL
