@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: alm2map + map2alm round trips at lmax = mmax = 4096 on HEALPix
+Nside = 2048 (50,331,648 pixels), a batch of maps per step, FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = sht_alm2map of B maps followed by sht_map2alm of the result
+(B = --maps, default 16).  `value` is maps per second (round trips) over the
+whole job with inputs resident in HBM; `e2e` is the same metric with the
+host->device copy of each step's a_lm (pinned) and the device->host read of
+its result inside the timed region.  For N > 1 (torchrun) every rank runs an
+independent replica of the workload; the barrier-bracketed time is the max
+over ranks.  `--impl reference` times the CPU oracle on this host's cores on
+bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ℓmax=4096 alm2map+map2alm maps/s, served vs plain; p99 ms; % FP64/TC peak"
+DATA = "synthetic: seeded complex Gaussian a_lm with C_l = 1/(l(l+1)+1), a_l0 real (CMB-like)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nside", type=int, default=2048)
+    ap.add_argument("--lmax", type=int, default=4096)
+    ap.add_argument("--maps", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return ("alm2map then map2alm round trip, HEALPix Nside=%d (%d px, %d rings), lmax=mmax=%d, "
+            "%d maps per step, plain FP64" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps))
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle on bounded samples
+
+def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0):
+    """Time the oracle on `nrings_sample` rings of alm2map and `nm_sample` values of m of
+    map2alm; return (estimated seconds per map round trip, description, threads)."""
+    import numpy as np
+
+    import oracle
+    from oracle import geometry
+    from paper_1106_0159_gb300 import inputs
+
+    geom = geometry.healpix(nside)
+    R = len(geom[0])
+    a = inputs.gaussian_alm(lmax, lmax, seed=100)[0]
+    rings = [int((offset + (k + 0.5) * R / nrings_sample)) % R for k in range(nrings_sample)]
+    t0 = time.perf_counter()
+    oracle.alm2map_rings(geom, a, lmax, lmax, rings)
+    t1 = time.perf_counter()
+    s = inputs.white_map(int(np.sum(geom[0])), seed=101)[0]
+    ms = [int((offset * 7 + (k + 0.5) * (lmax + 1) / nm_sample)) % (lmax + 1) for k in range(nm_sample)]
+    t2 = time.perf_counter()
+    oracle.map2alm_ms(geom, s, lmax, ms)
+    t3 = time.perf_counter()
+    est = (t1 - t0) * R / nrings_sample + (t3 - t2) * (lmax + 1) / nm_sample
+    desc = ("oracle alm2map on %d of %d rings (%.1f s) + map2alm on %d of %d values of m (%.1f s), "
+            "scaled to one full round trip" % (nrings_sample, R, t1 - t0, nm_sample, lmax + 1, t3 - t2))
+    return est, desc
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def reference_arm(a, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nthr = host_threads()
+    per_step = []
+    desc = ""
+    for i in range(a.warmup + a.steps):
+        est, desc = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, offset=i)
+        if i >= a.warmup:
+            per_step.append(est)
+    mean_s = statistics.mean(per_step)
+    value = 1.0 / mean_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double oracle)", "data": DATA,
+        "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": a.lmax,
+                   "mmax": a.lmax, "maps_per_step": 1, "mode": "CPU oracle, bounded samples",
+                   "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "maps/s", "cores": nthr, "kind": "oracle",
+                         "sample": desc + " (last step)"},
+        "e2e": {"value": value, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def traffic_from_profiles(kernel_key):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel source is unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p)).get(kernel_key)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1106_0159_gb300", "csrc", rec.get("source", ""))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if sha != rec.get("source_sha256_16"):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def ours_arm(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1106_0159_gb300 import inputs, sht
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sht.load()
+    peak_tf = sht.fp64_fma_tflops()
+    geom = sht.healpix_geometry(a.nside)
+    t0 = time.perf_counter()
+    plan = sht.Plan(geom, a.lmax, a.lmax, grid=sht.GRID_HEALPIX)
+    plan_s = time.perf_counter() - t0
+    B, L = a.maps, a.lmax
+    nalm, npix = plan.nalm, plan.npix
+    host_alm = torch.from_numpy(inputs.gaussian_alm(L, L, seed=1000 + rank, nmaps=B)).pin_memory()
+    alm = host_alm.cuda()
+    mp = torch.empty((B, npix), dtype=torch.float64, device="cuda")
+    alm_out = torch.empty((B, nalm), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.alm2map(alm, out=mp)
+        plan.map2alm(mp, out=alm_out)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.set_stage_timing(True)
+    plan.stage_times(reset=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    evs[0].record(stream)
+    for i in range(a.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    stages = plan.stage_times(reset=True)
+    plan.set_stage_timing(False)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * a.steps / (total_ms * 1e-3)
+
+    # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory
+    e2e = None
+    if not a.no_e2e:
+        host_out = torch.empty((B, nalm), dtype=torch.complex128).pin_memory()
+
+        def e2e_step():
+            alm.copy_(host_alm, non_blocking=True)
+            plan.alm2map(alm, out=mp)
+            plan.map2alm(mp, out=alm_out)
+            host_out.copy_(alm_out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        nbytes = B * nalm * 16
+        e2e = {"value": world * B * a.steps / (ems * 1e-3), "unit": "maps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # roofline of the dominant stage (FP64 pipe): nominal 3 flops per (l, m, ring-pair) step for the
+    # recurrence of each launch plus 4 flops per step per map for the accumulation
+    S = sum(L - m + 1 for m in range(L + 1)) * plan.npairs
+    legendre = {k: v for k, v in stages.items() if k in ("legendre_synth", "legendre_anal")}
+    dom = max(legendre, key=lambda k: legendre[k][0])
+    dom_ms, dom_launches = legendre[dom]
+    flops = S * (3.0 * dom_launches + 4.0 * B * a.steps)
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    kernel_key = "legendre_anal_kernel" if dom == "legendre_anal" else "legendre_synth_kernel"
+    traffic = traffic_from_profiles(kernel_key)
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": kernel_key, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic,
+                "peak_source": "FP64 FMA microbenchmark run in this process (sht_fp64_fma_tflops)",
+                "work": "7 flops per (l, m, ring-pair) step over the full triangle, per map (3 recurrence "
+                        "+ 4 accumulate); the kernel skips steps whose lambda is below 2^-224, so frac "
+                        "can exceed 1"}
+    launches = sum(v[1] for v in stages.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nthr = host_threads()
+        est, desc = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1)
+        cpu = {"value": 1.0 / est, "unit": "maps/s", "cores": nthr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        q = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": DATA,
+            "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": L, "mmax": L,
+                       "maps_per_step": B, "mode": "plain FP64", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (a_lm %.2f GB, maps %.2f GB per step)"
+                             % (B * nalm * 16 / 1e9, B * npix * 8 / 1e9),
+                       "plan_create_s": plan_s},
+            "latency_ms": {"p50": statistics.median(q), "p99": q[min(len(q) - 1, int(0.99 * len(q)))],
+                           "per": "step (%d-map round trip)" % B},
+            "roofline": roofline,
+            "stages_ms_per_step": {k: v[0] / a.steps for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if a.impl == "reference":
+        return reference_arm(a, rank, world)
+    return ours_arm(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,6 +120,25 @@ sht_status sht_geom_healpix(int nside, int64_t *nphi, double *theta, double *phi
 sht_status sht_geom_gauss_legendre(int nrings, int64_t nphi, int64_t *nphi_out, double *theta,
                                    double *phi0, double *w);
 
+/*
+ * Per-stage accounting.  Kernel launches are always counted; with timing
+ * enabled, every stage of every transform call is bracketed by CUDA events
+ * recorded on the call's stream.  Stage ids: 0 Legendre synthesis,
+ * 1 ring synthesis, 2 ring analysis, 3 Legendre analysis, 4 ring-block
+ * reduction of the analysis.  sht_plan_stage_times waits for the recorded
+ * events, adds their durations to the running totals, and writes the totals
+ * (ms[5], launches[5]); reset != 0 zeroes the totals afterwards.
+ */
+sht_status sht_plan_set_stage_timing(sht_plan_t plan, int enable);
+sht_status sht_plan_stage_times(sht_plan_t plan, double *ms, int64_t *launches, int reset);
+
+/*
+ * Calibration (not part of the transforms): FP64 FMA throughput of the
+ * current device in TFLOP/s (2 flops per FMA), from a short kernel of
+ * independent FMA chains; the denominator of the Legendre stage's roofline.
+ */
+sht_status sht_fp64_fma_tflops(double *tflops);
+
 const char *sht_status_string(sht_status s);
 const char *sht_plan_last_error(sht_plan_t plan);     /* "" when none */
 

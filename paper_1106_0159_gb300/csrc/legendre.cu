@@ -409,8 +409,10 @@ int anal_slots_per_cta(const Plan &p) { return p.nslots >= 4 * ANA_T ? 4 * ANA_T
 
 }  // namespace
 
-cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st)
+cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
+                                  int *nlaunch)
 {
+    *nlaunch = 0;
     SynArgs A;
     A.slotN = p.d_slotN;
     A.slotS = p.d_slotS;
@@ -441,6 +443,7 @@ cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *de
             legendre_synth_kernel<1><<<grid, SYN_T, 0, st>>>(A);
             g0 += 1;
         }
+        ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -454,9 +457,16 @@ size_t legendre_anal_partial_bytes(const Plan &p, int nmaps)
     return (size_t)nblk * (size_t)nmaps * (size_t)p.nalm * sizeof(double2);
 }
 
-cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
-                                 cudaStream_t st)
+int legendre_anal_nblk(const Plan &p)
 {
+    const int per = anal_slots_per_cta(p);
+    return (p.nslots + per - 1) / per;
+}
+
+cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *partial, int nmaps, cudaStream_t st,
+                                 int *nlaunch)
+{
+    *nlaunch = 0;
     const int per = anal_slots_per_cta(p);
     AnaArgs A;
     A.slotN = p.d_slotN;
@@ -492,13 +502,19 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *a
                 legendre_anal_kernel<1, 1><<<grid, ANA_T, 0, st>>>(A);
             g0 += 1;
         }
+        ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *alm, int nmaps, cudaStream_t st)
+{
     const int64_t total = p.nalm * nmaps;
-    int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    reduce_blocks_kernel<<<rgrid, 256, 0, st>>>(partial, p.d_cfac, alm, A.nblk, p.nalm, nmaps, p.lmax,
-                                                A.part_blk_stride);
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    reduce_blocks_kernel<<<rgrid, 256, 0, st>>>(partial, p.d_cfac, alm, legendre_anal_nblk(p), p.nalm, nmaps, p.lmax,
+                                                (int64_t)nmaps * p.nalm);
     return cudaGetLastError();
 }
 

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(FFT_T) bluestein_filter_kernel(const FftLen *l
                                                                  double2 *tab, double2 *scratch, int maxlen)
 {
     double2 *B0 = scratch + (int64_t)blockIdx.x * 3 * maxlen;
-    double2 *B1 = B0 + maxlen, *B2 = B1 + maxlen;
+    double2 *B1 = B0 + maxlen;
     for (int t = blockIdx.x; t < nids; t += gridDim.x) {
         const FftLen &F = lens[ids[t]];
         const int n = F.n, M = F.M;
@@ -319,7 +319,6 @@ __global__ void __launch_bounds__(FFT_T) bluestein_filter_kernel(const FftLen *l
         }
         __syncthreads();
     }
-    (void)B2;
 }
 
 // exp(i m phi0_r), with m phi0 reduced modulo 2 pi in extra precision

@@ -70,13 +70,28 @@ struct Plan {
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
 
+    // per-stage accounting: launches always, device time when enabled
+    enum { NSTAGE = 5 };
+    bool timing = false;
+    int64_t launches[NSTAGE] = {0, 0, 0, 0, 0};
+    double stage_ms[NSTAGE] = {0, 0, 0, 0, 0};
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+
     std::string last_error;
 };
 
-// launch helpers (legendre.cu, ringfft.cu); return cudaGetLastError()
-cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st);
-cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
-                                 cudaStream_t st);
+// launch helpers (legendre.cu, ringfft.cu); return cudaGetLastError(), count launches in *nlaunch
+cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
+                                  int *nlaunch);
+cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *partial, int nmaps, cudaStream_t st,
+                                 int *nlaunch);
+cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *alm, int nmaps, cudaStream_t st);
+int legendre_anal_nblk(const Plan &p);
 size_t legendre_anal_partial_bytes(const Plan &p, int nmaps);
 cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                               cudaStream_t st);

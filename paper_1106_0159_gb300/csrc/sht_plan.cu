@@ -172,9 +172,99 @@ sht_status check_call(sht_plan_t plan, const void *in, const void *out, int nmap
     return SHT_OK;
 }
 
-sht_status after_launch(Plan &p, cudaError_t e, const char *where)
+
+
+// --- stage runners: launches plus optional event bracketing on the call's stream
+cudaEvent_t pool_event(Plan &p)
 {
-    if (e != cudaSuccess) return cuda_fail(p, e, where);
+    if (!p.event_pool.empty()) {
+        cudaEvent_t e = p.event_pool.back();
+        p.event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+struct StageScope {
+    Plan &p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageScope(Plan &pl, int st, cudaStream_t str) : p(pl), stage(st), s(str)
+    {
+        if (p.timing) {
+            a = pool_event(p);
+            b = pool_event(p);
+            if (a && b) cudaEventRecord(a, s);
+        }
+    }
+    void done()
+    {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            p.pending.push_back({stage, a, b});
+            a = b = nullptr;
+        }
+    }
+    ~StageScope()
+    {
+        if (a) p.event_pool.push_back(a);
+        if (b) p.event_pool.push_back(b);
+    }
+};
+
+sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t s)
+{
+    StageScope sc(p, 0, s);
+    int n = 0;
+    cudaError_t e = sht::launch_legendre_synth(p, alm, delta, nmaps, s, &n);
+    p.launches[0] += n;
+    if (e != cudaSuccess) return cuda_fail(p, e, "legendre_synth");
+    sc.done();
+    return SHT_OK;
+}
+
+sht_status run_ring_synth(Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps, cudaStream_t s)
+{
+    StageScope sc(p, 1, s);
+    cudaError_t e = sht::launch_ring_synth(p, delta, map, scratch, nmaps, s);
+    p.launches[1] += 1;
+    if (e != cudaSuccess) return cuda_fail(p, e, "ring_synth");
+    sc.done();
+    return SHT_OK;
+}
+
+sht_status run_ring_anal(Plan &p, const double *map, double2 *delta, double2 *scratch, int nmaps, cudaStream_t s)
+{
+    StageScope sc(p, 2, s);
+    cudaError_t e = sht::launch_ring_anal(p, map, delta, scratch, nmaps, s);
+    p.launches[2] += 1;
+    if (e != cudaSuccess) return cuda_fail(p, e, "ring_anal");
+    sc.done();
+    return SHT_OK;
+}
+
+sht_status run_legendre_anal(Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
+                             cudaStream_t s)
+{
+    {
+        StageScope sc(p, 3, s);
+        int n = 0;
+        cudaError_t e = sht::launch_legendre_anal(p, delta, partial, nmaps, s, &n);
+        p.launches[3] += n;
+        if (e != cudaSuccess) return cuda_fail(p, e, "legendre_anal");
+        sc.done();
+    }
+    StageScope sc(p, 4, s);
+    cudaError_t e = sht::launch_block_reduce(p, partial, alm, nmaps, s);
+    p.launches[4] += 1;
+    if (e != cudaSuccess) return cuda_fail(p, e, "block_reduce");
+    sc.done();
     return SHT_OK;
 }
 
@@ -303,6 +393,11 @@ void sht_plan_destroy(sht_plan_t plan)
 {
     if (!plan) return;
     cudaDeviceSynchronize();
+    for (auto &pe : plan->p.pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : plan->p.event_pool) cudaEventDestroy(e);
     free_plan_device(plan->p);
     delete plan;
 }
@@ -312,10 +407,7 @@ sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int
     sht_status st = check_call(plan, alm, delta, nmaps);
     if (st != SHT_OK || nmaps == 0) return st;
     Plan &p = plan->p;
-    return after_launch(p,
-                        sht::launch_legendre_synth(p, (const double2 *)alm, (double2 *)delta, nmaps,
-                                                   (cudaStream_t)stream),
-                        "legendre_synth");
+    return run_legendre_synth(p, (const double2 *)alm, (double2 *)delta, nmaps, (cudaStream_t)stream);
 }
 
 sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int nmaps, void *stream)
@@ -325,10 +417,7 @@ sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int n
     Plan &p = plan->p;
     st = ensure_workspace(p, align256(sht::ring_scratch_bytes(p)));
     if (st != SHT_OK) return st;
-    return after_launch(p,
-                        sht::launch_ring_synth(p, (const double2 *)delta, map, (double2 *)p.d_ws, nmaps,
-                                               (cudaStream_t)stream),
-                        "ring_synth");
+    return run_ring_synth(p, (const double2 *)delta, map, (double2 *)p.d_ws, nmaps, (cudaStream_t)stream);
 }
 
 sht_status sht_ring_anal(sht_plan_t plan, const double *map, void *delta, int nmaps, void *stream)
@@ -338,10 +427,7 @@ sht_status sht_ring_anal(sht_plan_t plan, const double *map, void *delta, int nm
     Plan &p = plan->p;
     st = ensure_workspace(p, align256(sht::ring_scratch_bytes(p)));
     if (st != SHT_OK) return st;
-    return after_launch(p,
-                        sht::launch_ring_anal(p, map, (double2 *)delta, (double2 *)p.d_ws, nmaps,
-                                              (cudaStream_t)stream),
-                        "ring_anal");
+    return run_ring_anal(p, map, (double2 *)delta, (double2 *)p.d_ws, nmaps, (cudaStream_t)stream);
 }
 
 sht_status sht_legendre_anal(sht_plan_t plan, const void *delta, void *alm, int nmaps, void *stream)
@@ -351,10 +437,8 @@ sht_status sht_legendre_anal(sht_plan_t plan, const void *delta, void *alm, int 
     Plan &p = plan->p;
     st = ensure_workspace(p, align256(sht::legendre_anal_partial_bytes(p, nmaps)));
     if (st != SHT_OK) return st;
-    return after_launch(p,
-                        sht::launch_legendre_anal(p, (const double2 *)delta, (double2 *)alm, (double2 *)p.d_ws,
-                                                  nmaps, (cudaStream_t)stream),
-                        "legendre_anal");
+    return run_legendre_anal(p, (const double2 *)delta, (double2 *)alm, (double2 *)p.d_ws, nmaps,
+                             (cudaStream_t)stream);
 }
 
 sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream)
@@ -368,9 +452,9 @@ sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps,
     double2 *delta = (double2 *)p.d_ws;
     double2 *scratch = (double2 *)((char *)p.d_ws + d);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = sht::launch_legendre_synth(p, (const double2 *)alm, delta, nmaps, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "legendre_synth");
-    return after_launch(p, sht::launch_ring_synth(p, delta, map, scratch, nmaps, s), "ring_synth");
+    st = run_legendre_synth(p, (const double2 *)alm, delta, nmaps, s);
+    if (st != SHT_OK) return st;
+    return run_ring_synth(p, delta, map, scratch, nmaps, s);
 }
 
 sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream)
@@ -386,9 +470,45 @@ sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps,
     double2 *delta = (double2 *)p.d_ws;
     double2 *scratch = (double2 *)((char *)p.d_ws + d);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = sht::launch_ring_anal(p, map, delta, scratch, nmaps, s);
-    if (e != cudaSuccess) return cuda_fail(p, e, "ring_anal");
-    return after_launch(p, sht::launch_legendre_anal(p, delta, (double2 *)alm, scratch, nmaps, s), "legendre_anal");
+    st = run_ring_anal(p, map, delta, scratch, nmaps, s);
+    if (st != SHT_OK) return st;
+    return run_legendre_anal(p, delta, (double2 *)alm, scratch, nmaps, s);
+}
+
+sht_status sht_plan_set_stage_timing(sht_plan_t plan, int enable)
+{
+    if (!plan) return SHT_EINVAL;
+    plan->p.timing = enable != 0;
+    return SHT_OK;
+}
+
+sht_status sht_plan_stage_times(sht_plan_t plan, double *ms, int64_t *launches, int reset)
+{
+    if (!plan) return SHT_EINVAL;
+    Plan &p = plan->p;
+    sht_status st = SHT_OK;
+    for (auto &pe : p.pending) {
+        cudaError_t e = cudaEventSynchronize(pe.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pe.a, pe.b);
+        if (e != cudaSuccess) {
+            st = cuda_fail(p, e, "stage timing");
+        } else {
+            p.stage_ms[pe.stage] += t;
+        }
+        p.event_pool.push_back(pe.a);
+        p.event_pool.push_back(pe.b);
+    }
+    p.pending.clear();
+    for (int i = 0; i < Plan::NSTAGE; ++i) {
+        if (ms) ms[i] = p.stage_ms[i];
+        if (launches) launches[i] = p.launches[i];
+        if (reset) {
+            p.stage_ms[i] = 0.0;
+            p.launches[i] = 0;
+        }
+    }
+    return st;
 }
 
 // ------------------------------------------------------------------ grids

@@ -32,8 +32,10 @@ EXPORTS = (
     "sht_legendre_synth", "sht_ring_synth", "sht_ring_anal", "sht_legendre_anal",
     "sht_nalm", "sht_alm_index", "sht_plan_npix", "sht_plan_nrings", "sht_plan_npairs",
     "sht_workspace_bytes", "sht_geom_healpix", "sht_geom_gauss_legendre",
-    "sht_status_string", "sht_plan_last_error",
+    "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
+    "sht_fp64_fma_tflops",
 )
+STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
 
 
 class ShtError(RuntimeError):
@@ -76,6 +78,9 @@ def load():
             "sht_geom_gauss_legendre": (I, [I, I64, P, P, P, P]),
             "sht_status_string": (ctypes.c_char_p, [I]),
             "sht_plan_last_error": (ctypes.c_char_p, [P]),
+            "sht_plan_set_stage_timing": (I, [P, I]),
+            "sht_plan_stage_times": (I, [P, P, P, I]),
+            "sht_fp64_fma_tflops": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -135,6 +140,13 @@ def gauss_legendre_geometry(nrings: int, nphi: int):
     return n, th, p0, w
 
 
+def fp64_fma_tflops() -> float:
+    """Measured FP64 FMA throughput of the current GPU (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(load().sht_fp64_fma_tflops(ctypes.byref(v)), what="sht_fp64_fma_tflops")
+    return float(v.value)
+
+
 def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -183,6 +195,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_stage_timing(self, enable: bool):
+        _check(load().sht_plan_set_stage_timing(self._h, 1 if enable else 0), self._h)
+
+    def stage_times(self, reset: bool = False):
+        """{stage: (ms, launches)} accumulated since the last reset (waits for the recorded events)."""
+        ms = np.zeros(5, np.float64)
+        nl = np.zeros(5, np.int64)
+        _check(load().sht_plan_stage_times(self._h, _np_ptr(ms), _np_ptr(nl), 1 if reset else 0), self._h)
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(STAGES)}
 
     def workspace_bytes(self, nmaps: int) -> int:
         return int(load().sht_workspace_bytes(self._h, int(nmaps)))
