@@ -201,15 +201,11 @@ def ours_arm(a, rank, world, local_rank):
 
     from paper_1106_0159_gb300 import inputs, sht
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1106_0159_gb300.replicas import Replicas, job_throughput
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    torch.cuda.set_device(local_rank)
+    rep = Replicas(device=torch.device("cuda", local_rank))
+    barrier = rep.barrier
 
     sht.load()
     peak_tf = sht.fp64_fma_tflops()
@@ -219,7 +215,7 @@ def ours_arm(a, rank, world, local_rank):
     plan_s = time.perf_counter() - t0
     B, L = a.maps, a.lmax
     nalm, npix = plan.nalm, plan.npix
-    host_alm = torch.from_numpy(inputs.gaussian_alm(L, L, seed=1000 + rank, nmaps=B)).pin_memory()
+    host_alm = torch.from_numpy(inputs.gaussian_alm(L, L, seed=rep.seed(1000), nmaps=B)).pin_memory()
     alm = host_alm.cuda()
     mp = torch.empty((B, npix), dtype=torch.float64, device="cuda")
     alm_out = torch.empty((B, nalm), dtype=torch.complex128, device="cuda")
@@ -251,11 +247,8 @@ def ours_arm(a, rank, world, local_rank):
     total_ms = evs[0].elapsed_time(evs[-1])
     stages = plan.stage_times(reset=True)
     plan.set_stage_timing(False)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * a.steps / (total_ms * 1e-3)
+    total_ms = rep.max_over_ranks(total_ms, device="cuda")
+    value = job_throughput(world, B * a.steps, total_ms)
 
     # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory
     e2e = None
@@ -278,13 +271,9 @@ def ours_arm(a, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = rep.max_over_ranks(e0.elapsed_time(e1), device="cuda")
         nbytes = B * nalm * 16
-        e2e = {"value": world * B * a.steps / (ems * 1e-3), "unit": "maps/s",
+        e2e = {"value": job_throughput(world, B * a.steps, ems), "unit": "maps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     # roofline of the dominant stage (FP64 pipe): nominal 3 flops per (l, m, ring-pair) step for the
@@ -334,8 +323,7 @@ def ours_arm(a, rank, world, local_rank):
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 

@@ -30,6 +30,20 @@
 // once every 16 steps.  Terms are accumulated only at k = 0; terms with
 // k < 0 are below 2^-224 and are dropped.  Once a whole warp has k = 0 the
 // loop carries no tests at all.
+//
+// Polar slots.  Near a pole x = cos(theta) -> 1 and the recurrence is close
+// to degenerate: a rounding error of relative size eps in y excites the
+// second solution with amplitude ~eps/sin(theta), and over n steps the
+// error in lambda grows to ~eps n^1.5 (1e-10 at theta = 4e-4, l = 4096).
+// CTAs whose first slot has sin(theta) < 0.03 therefore run, for
+// m <= mR, Reinsch's difference form in lambda itself:
+//     D_l = (1 + rho_l) D_{l-1} + g_l lambda_{l-1},  lambda_l = lambda_{l-1} + D_l,
+//     g_l = (beta_l - 2 - rho_l) - beta_l u,  rho_l = beta_l / beta_{l-1} - 1,
+// with rho_l and b0_l = beta_l - 2 - rho_l tabulated from cancellation-free
+// formulas; rounding errors then act on the small difference D instead of on
+// lambda.  It costs four FP64 instructions per step instead of two.  For
+// m > mR the values on these rings stay below the rescaling threshold for
+// every l <= lmax, so the y form is used there.
 #include "sht_internal.h"
 
 #include <algorithm>
@@ -43,6 +57,7 @@ constexpr int CHL = 128;        // l-values staged per shared-memory chunk (mult
 constexpr int SUB = 16;         // steps between rescale tests
 constexpr int RESCALE_THR = 1023 + 256;  // biased exponent that triggers a rescale
 constexpr int RED_CL = 8;       // l-values per warp reduction round (analysis)
+constexpr double POLAR_SIN = 0.03;  // CTAs starting below this sin(theta) use the Reinsch form
 
 __device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
@@ -92,24 +107,67 @@ __device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
     k = kk;
 }
 
+// Recurrence coefficients of one l-chunk in shared memory.
+struct Coef {
+    double al[CHL];               // y form: alpha_l
+    double be[CHL], rh[CHL], b0[CHL];  // Reinsch form: beta_l, rho_l, b0_l
+};
+
+// One step of the recurrence.  y1 is the newest value; y2 is the previous
+// value (y form) or the last difference D (Reinsch form).
+template <bool REIN>
+__device__ __forceinline__ double rec_step(const Coef &C, int j, double u, double &y1, double &y2)
+{
+    if (REIN) {
+        const double g = fma(-C.be[j], u, C.b0[j]);
+        const double t = fma(g, y1, y2);
+        y2 = fma(C.rh[j], y2, t);
+        y1 = y1 + y2;
+        return y1;
+    } else {
+        const double t = fma(-u, y1, y1);
+        const double y = fma(C.al[j], t, -y2);
+        y2 = y1;
+        y1 = y;
+        return y;
+    }
+}
+
+// State before l = m that makes the first two steps produce lambda_m and lambda_{m+1}.
+template <bool REIN>
+__device__ __forceinline__ void seed_state(double y0, double &y1, double &y2)
+{
+    y1 = 0.0;                  // value at l = m - 1
+    y2 = REIN ? y0 : -y0;      // D_{m-1} = lambda_m (Reinsch) or y_{m-2} = -y_m
+}
+
+template <bool REIN>
+__device__ __forceinline__ void stage_coef(Coef &C, const double *alpha, const double3 *rein, int64_t ix, int i)
+{
+    if (REIN) {
+        const double3 c = rein[ix];
+        C.be[i] = c.x;
+        C.rh[i] = c.y;
+        C.b0[i] = c.z;
+    } else {
+        C.al[i] = alpha[ix];
+    }
+}
+
 struct SynArgs {
     const double2 *alm;   // [nmaps][nalm], first map of this launch
     double2 *delta;       // [nmaps][nrings][mmax+1]
     const int *slotN, *slotS;
     const double *u, *s;
     const double *alpha, *cfac;
-    int nslots, nblk, lmax, mmax, nrings;
+    const double3 *rein;  // Reinsch coefficients for m <= mR
+    int nslots, nblk, lmax, mmax, nrings, mR;
     int64_t nalm;
 };
 
-template <int NM>
-__global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
+template <int NM, bool REIN>
+__device__ __forceinline__ void synth_body(const SynArgs &A, int m, int blk, Coef &C, double2 (*s_a)[CHL])
 {
-    __shared__ double s_al[CHL];
-    __shared__ double2 s_a[NM][CHL];
-
-    const int m = blockIdx.x / A.nblk;
-    const int blk = blockIdx.x - m * A.nblk;
     const int slot = blk * SYN_T + threadIdx.x;
     const bool active = slot < A.nslots;
     const int L = A.lmax;
@@ -121,8 +179,7 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
         u = A.u[slot];
         double y0;
         sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
-        y1 = 0.0;     // y_{m-1}
-        y2 = -y0;     // y_{m-2} := -y_m, so the first step yields y_m
+        seed_state<REIN>(y0, y1, y2);
     }
 
     double Er[NM], Ei[NM], Or[NM], Oi[NM];
@@ -134,8 +191,8 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
         __syncthreads();
         for (int i = threadIdx.x; i < nl; i += SYN_T) {
             const int64_t ix = base + (l0 - m) + i;
-            s_al[i] = A.alpha[ix];
-            const double c = A.cfac[ix];
+            stage_coef<REIN>(C, A.alpha, A.rein, ix, i);
+            const double c = REIN ? 1.0 : A.cfac[ix];  // the y form sums c_l a_l y_l
 #pragma unroll
             for (int g = 0; g < NM; ++g) {
                 double2 a = A.alm[(int64_t)g * A.nalm + ix];
@@ -150,20 +207,14 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
             if (!scaled) {
                 int j = j0;
                 for (; j + 1 < jn; j += 2) {
-                    double t = fma(-u, y1, y1);
-                    double y = fma(s_al[j], t, -y2);
-                    y2 = y1;
-                    y1 = y;
+                    double y = rec_step<REIN>(C, j, u, y1, y2);
 #pragma unroll
                     for (int g = 0; g < NM; ++g) {
                         const double2 a = s_a[g][j];
                         Er[g] = fma(a.x, y, Er[g]);
                         Ei[g] = fma(a.y, y, Ei[g]);
                     }
-                    t = fma(-u, y1, y1);
-                    y = fma(s_al[j + 1], t, -y2);
-                    y2 = y1;
-                    y1 = y;
+                    y = rec_step<REIN>(C, j + 1, u, y1, y2);
 #pragma unroll
                     for (int g = 0; g < NM; ++g) {
                         const double2 a = s_a[g][j + 1];
@@ -172,10 +223,7 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
                     }
                 }
                 if (j < jn) {  // ragged end: one even step
-                    double t = fma(-u, y1, y1);
-                    double y = fma(s_al[j], t, -y2);
-                    y2 = y1;
-                    y1 = y;
+                    const double y = rec_step<REIN>(C, j, u, y1, y2);
 #pragma unroll
                     for (int g = 0; g < NM; ++g) {
                         const double2 a = s_a[g][j];
@@ -186,10 +234,7 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
             } else {
                 const bool any_live = __any_sync(0xffffffffu, active && k == 0);
                 for (int j = j0; j < jn; ++j) {
-                    double t = fma(-u, y1, y1);
-                    double y = fma(s_al[j], t, -y2);
-                    y2 = y1;
-                    y1 = y;
+                    const double y = rec_step<REIN>(C, j, u, y1, y2);
                     if (any_live) {
                         const double ya = (k == 0) ? y : 0.0;
                         if (((j + l0 - m) & 1) == 0) {
@@ -230,13 +275,28 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
     }
 }
 
+template <int NM>
+__global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
+{
+    __shared__ Coef C;
+    __shared__ double2 s_a[NM][CHL];
+    const int m = blockIdx.x / A.nblk;
+    const int blk = blockIdx.x - m * A.nblk;
+    const bool polar = m <= A.mR && A.s[blk * SYN_T] < POLAR_SIN;  // slots are sorted by colatitude
+    if (polar)
+        synth_body<NM, true>(A, m, blk, C, s_a);
+    else
+        synth_body<NM, false>(A, m, blk, C, s_a);
+}
+
 struct AnaArgs {
     const double2 *delta;  // [nmaps][nrings][mmax+1], first map of this launch
     double2 *partial;      // [nblk][nmaps_total][nalm]
     const int *slotN, *slotS;
     const double *u, *s;
-    const double *alpha;
-    int nslots, nblk, lmax, mmax, nrings;
+    const double *alpha, *cfac;
+    const double3 *rein;
+    int nslots, nblk, lmax, mmax, nrings, mR;
     int64_t nalm;
     int64_t part_map_stride;   // nalm
     int64_t part_blk_stride;   // nmaps_total * nalm
@@ -263,15 +323,11 @@ __device__ __forceinline__ double warp_reduce_scatter8(double v[RED_CL])
     return r;
 }
 
-template <int NM, int K>
-__global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
+template <int NM, int K, bool REIN>
+__device__ __forceinline__ void anal_body(const AnaArgs &A, int m, int blk, Coef &C,
+                                          double (*s_red)[CHL][2 * NM])
 {
     constexpr int NW = ANA_T / 32;
-    __shared__ double s_al[CHL];
-    __shared__ double s_red[NW][CHL][2 * NM];
-
-    const int m = blockIdx.x / A.nblk;
-    const int blk = blockIdx.x - m * A.nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
@@ -279,6 +335,7 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
 
     double u[K], y1[K], y2[K];
     int k[K];
+    bool act[K];
     double Sr[K][NM], Si[K][NM], Dr[K][NM], Di[K][NM];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
@@ -287,13 +344,14 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
         y1[q] = 0.0;
         y2[q] = 0.0;
         k[q] = 0;
+        act[q] = slot < A.nslots;
 #pragma unroll
         for (int g = 0; g < NM; ++g) Sr[q][g] = Si[q][g] = Dr[q][g] = Di[q][g] = 0.0;
-        if (slot < A.nslots) {
+        if (act[q]) {
             u[q] = A.u[slot];
             double y0;
             sectoral_start(A.s[slot], A.alpha[base], m, y0, k[q]);
-            y2[q] = -y0;
+            seed_state<REIN>(y0, y1[q], y2[q]);
             const int rn = A.slotN[slot], rs = A.slotS[slot];
 #pragma unroll
             for (int g = 0; g < NM; ++g) {
@@ -312,7 +370,7 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
     for (int l0 = m; l0 <= L; l0 += CHL) {
         const int nl = min(CHL, L - l0 + 1);
         __syncthreads();
-        for (int i = threadIdx.x; i < nl; i += ANA_T) s_al[i] = A.alpha[base + (l0 - m) + i];
+        for (int i = threadIdx.x; i < nl; i += ANA_T) stage_coef<REIN>(C, A.alpha, A.rein, base + (l0 - m) + i, i);
         __syncthreads();
 
         for (int j0 = 0; j0 < nl; j0 += SUB) {
@@ -320,42 +378,62 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
 #pragma unroll
             for (int q = 0; q < K; ++q) scaled |= (k[q] < 0);
             scaled = __any_sync(0xffffffffu, scaled);
-            // two rounds of RED_CL l-values per SUB block
+            // While every slot of the warp is still below the rescaling threshold its
+            // terms are all dropped: only the recurrence runs and the warp's partial
+            // sums for these l are zero.
+            bool live = true;
+            if (scaled) {
+                bool mine = false;
 #pragma unroll
-            for (int h = 0; h < SUB / RED_CL; ++h) {
-                const int jb = j0 + h * RED_CL;
-                double vr[NM][RED_CL], vi[NM][RED_CL];
+                for (int q = 0; q < K; ++q) mine |= (act[q] && k[q] == 0);
+                live = __any_sync(0xffffffffu, mine);
+            }
+            if (!live) {
+                for (int j = j0; j < min(j0 + SUB, nl); ++j) {
 #pragma unroll
-                for (int jj = 0; jj < RED_CL; ++jj) {
-                    const int j = jb + jj;
-                    const double al = (j < nl) ? s_al[j] : 0.0;
-                    const bool even = ((jj & 1) == 0);  // jb - 0 is even: l0 - m and j0, jb are even
+                    for (int q = 0; q < K; ++q) rec_step<REIN>(C, j, u[q], y1[q], y2[q]);
+                }
+                if (lane < SUB) {
 #pragma unroll
-                    for (int g = 0; g < NM; ++g) vr[g][jj] = vi[g][jj] = 0.0;
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const double t = fma(-u[q], y1[q], y1[q]);
-                        double y = fma(al, t, -y2[q]);
-                        if (j >= nl) y = y1[q] * 0.0;  // past the end: keep the state (no-op step)
-                        if (j < nl) {
-                            y2[q] = y1[q];
-                            y1[q] = y;
-                        }
-                        if (scaled) y = (k[q] == 0) ? y : 0.0;
-#pragma unroll
-                        for (int g = 0; g < NM; ++g) {
-                            vr[g][jj] = fma(y, even ? Sr[q][g] : Dr[q][g], vr[g][jj]);
-                            vi[g][jj] = fma(y, even ? Si[q][g] : Di[q][g], vi[g][jj]);
-                        }
+                    for (int g = 0; g < NM; ++g) {
+                        s_red[warp][j0 + lane][2 * g] = 0.0;
+                        s_red[warp][j0 + lane][2 * g + 1] = 0.0;
                     }
                 }
+            } else {
+                // two rounds of RED_CL l-values per SUB block
 #pragma unroll
-                for (int g = 0; g < NM; ++g) {
-                    const double rr = warp_reduce_scatter8(vr[g]);
-                    const double ri = warp_reduce_scatter8(vi[g]);
-                    if (lane < RED_CL && jb + lane < CHL) {
-                        s_red[warp][jb + lane][2 * g] = rr;
-                        s_red[warp][jb + lane][2 * g + 1] = ri;
+                for (int h = 0; h < SUB / RED_CL; ++h) {
+                    const int jb = j0 + h * RED_CL;
+                    double vr[NM][RED_CL], vi[NM][RED_CL];
+#pragma unroll
+                    for (int jj = 0; jj < RED_CL; ++jj) {
+                        const int j = jb + jj;
+                        const bool inside = j < nl;
+                        const bool even = ((jj & 1) == 0);  // l - m has the parity of jj
+#pragma unroll
+                        for (int g = 0; g < NM; ++g) vr[g][jj] = vi[g][jj] = 0.0;
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            double y = 0.0;
+                            if (inside) y = rec_step<REIN>(C, j, u[q], y1[q], y2[q]);
+                            const bool use = inside && (!scaled || k[q] == 0);
+                            y = use ? y : 0.0;
+#pragma unroll
+                            for (int g = 0; g < NM; ++g) {
+                                vr[g][jj] = fma(y, even ? Sr[q][g] : Dr[q][g], vr[g][jj]);
+                                vi[g][jj] = fma(y, even ? Si[q][g] : Di[q][g], vi[g][jj]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < NM; ++g) {
+                        const double rr = warp_reduce_scatter8(vr[g]);
+                        const double ri = warp_reduce_scatter8(vi[g]);
+                        if (lane < RED_CL) {
+                            s_red[warp][jb + lane][2 * g] = rr;
+                            s_red[warp][jb + lane][2 * g + 1] = ri;
+                        }
                     }
                 }
             }
@@ -371,7 +449,8 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
             }
         }
         __syncthreads();
-        // sum the warps and write this block's partial a_lm (times 1/c, applied later)
+        // sum the warps and write this block's partial a_lm; the reduction multiplies
+        // by c_l, so the Reinsch form (which sums lambda, not y) divides by it here
         for (int i = threadIdx.x; i < nl * NM; i += ANA_T) {
             const int j = i % nl, g = i / nl;
             double re = 0.0, im = 0.0;
@@ -380,10 +459,30 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
                 re += s_red[w][j][2 * g];
                 im += s_red[w][j][2 * g + 1];
             }
-            A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + base + (l0 - m) + j] =
-                make_double2(re, im);
+            const int64_t ix = base + (l0 - m) + j;
+            if (REIN) {
+                const double c = A.cfac[ix];
+                re /= c;
+                im /= c;
+            }
+            A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + ix] = make_double2(re, im);
         }
     }
+}
+
+template <int NM, int K>
+__global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
+{
+    constexpr int NW = ANA_T / 32;
+    __shared__ Coef C;
+    __shared__ double s_red[NW][CHL][2 * NM];
+    const int m = blockIdx.x / A.nblk;
+    const int blk = blockIdx.x - m * A.nblk;
+    const bool polar = m <= A.mR && A.s[blk * (ANA_T * K)] < POLAR_SIN;
+    if (polar)
+        anal_body<NM, K, true>(A, m, blk, C, s_red);
+    else
+        anal_body<NM, K, false>(A, m, blk, C, s_red);
 }
 
 // a_lm = c_lm * sum over ring blocks (fixed order), Im a_l0 = 0
@@ -420,6 +519,8 @@ cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *de
     A.s = p.d_s;
     A.alpha = p.d_alpha;
     A.cfac = p.d_cfac;
+    A.rein = p.d_rein;
+    A.mR = p.mR;
     A.nslots = p.nslots;
     A.nblk = (p.nslots + SYN_T - 1) / SYN_T;
     A.lmax = p.lmax;
@@ -474,6 +575,9 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *p
     A.u = p.d_u;
     A.s = p.d_s;
     A.alpha = p.d_alpha;
+    A.cfac = p.d_cfac;
+    A.rein = p.d_rein;
+    A.mR = p.mR;
     A.nslots = p.nslots;
     A.nblk = (p.nslots + per - 1) / per;
     A.lmax = p.lmax;

@@ -52,6 +52,8 @@ struct Plan {
     double *d_s = nullptr;      // sin(theta) per slot
     double *d_alpha = nullptr;  // [nalm] recurrence coefficients (see legendre.cu)
     double *d_cfac = nullptr;   // [nalm] lambda_lm = cfac * y_lm
+    int mR = -1;                // Reinsch-form tables cover m <= mR
+    double3 *d_rein = nullptr;  // [index(lmax, mR) + 1] (beta, rho, b0) for polar slots
     int64_t *d_ofs = nullptr;   // [nrings + 1]
     int *d_nphi = nullptr;      // [nrings]
     double *d_w = nullptr;      // [nrings]

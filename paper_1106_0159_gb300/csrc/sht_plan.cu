@@ -29,8 +29,8 @@ sht_status cuda_fail(Plan &p, cudaError_t e, const char *where)
 
 void free_plan_device(Plan &p)
 {
-    void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac, p.d_ofs,
-                    p.d_nphi,  p.d_w,     p.d_phase, p.d_items, p.d_lens,    p.d_fft_tab, p.d_ws};
+    void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
+                    p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -41,6 +41,7 @@ void free_plan_device(Plan &p)
     p.d_items = nullptr;
     p.d_lens = nullptr;
     p.d_fft_tab = nullptr;
+    p.d_rein = nullptr;
     p.d_ws = nullptr;
     p.ws_bytes = 0;
 }
@@ -136,6 +137,40 @@ void recurrence_tables(int lmax, int mmax, std::vector<double> &alpha, std::vect
             c2 = c1;
             c1 = c;
             bprev = b;
+        }
+    }
+}
+
+// Reinsch-form tables for polar slots, m <= mR: (beta_l, rho_l, b0_l) with
+// rho_l = beta_l / beta_{l-1} - 1 and b0_l = beta_l - 2 - rho_l, both from
+// cancellation-free forms: delta_l = beta_l - 2 = (4m^2 - 1) / ((l^2 - m^2)(beta_l + 2)),
+// rho_l = (delta_l - delta_{l-1}) / beta_{l-1}, b0_l = delta_l - rho_l.  Entries at
+// l = m and l = m+1 seed the recurrence (see legendre.cu).
+void reinsch_tables(int lmax, int mR, std::vector<double3> &rein)
+{
+    if (mR < 0) {
+        rein.clear();
+        return;
+    }
+    const int64_t n = sht_alm_index(lmax, lmax, mR) + 1;
+    rein.assign(n, make_double3(0.0, 0.0, 0.0));
+    for (int m = 0; m <= mR; ++m) {
+        const int64_t base = sht_alm_index(lmax, m, m);
+        rein[base] = make_double3(0.0, 0.0, 0.0);
+        if (m + 1 > lmax) continue;
+        const double b1 = std::sqrt(2.0 * m + 3.0);
+        rein[base + 1] = make_double3(b1, -1.0, b1 - 1.0);
+        const double m2 = (double)m * m, q = 4.0 * m2 - 1.0;
+        double bprev = b1;
+        double dprev = q / ((2.0 * m + 1.0) * (b1 + 2.0));  // beta_{m+1} - 2
+        for (int l = m + 2; l <= lmax; ++l) {
+            const double L = (double)l;
+            const double b = std::sqrt((4.0 * L * L - 1.0) / (L * L - m2));
+            const double d = q / ((L * L - m2) * (b + 2.0));
+            const double rho = (d - dprev) / bprev;
+            rein[base + (l - m)] = make_double3(b, rho, d - rho);
+            bprev = b;
+            dprev = d;
         }
     }
 }
@@ -354,6 +389,11 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     }
     std::vector<double> alpha, cfac;
     recurrence_tables(lmax, mmax, alpha, cfac);
+    bool any_polar = false;
+    for (int k = 0; k < p.nslots; ++k) any_polar |= (s[k] < 0.03);
+    p.mR = any_polar ? std::min(mmax, lmax / 10 + 64) : -1;
+    std::vector<double3> rein;
+    reinsch_tables(lmax, p.mR, rein);
     std::vector<int> nphi32(nrings);
     for (int r = 0; r < nrings; ++r) nphi32[r] = (int)nphi[r];
 
@@ -365,6 +405,7 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     if (e == cudaSuccess) e = upload(&p.d_s, s.data(), s.size());
     if (e == cudaSuccess) e = upload(&p.d_alpha, alpha.data(), alpha.size());
     if (e == cudaSuccess) e = upload(&p.d_cfac, cfac.data(), cfac.size());
+    if (e == cudaSuccess && p.mR >= 0) e = upload(&p.d_rein, rein.data(), rein.size());
     if (e == cudaSuccess) e = upload(&p.d_ofs, p.ofs.data(), p.ofs.size());
     if (e == cudaSuccess) e = upload(&p.d_nphi, nphi32.data(), nphi32.size());
     if (e == cudaSuccess) e = upload(&p.d_w, p.w.data(), p.w.size());
