@@ -139,6 +139,25 @@ sht_status sht_plan_stage_times(sht_plan_t plan, double *ms, int64_t *launches, 
  */
 sht_status sht_fp64_fma_tflops(double *tflops);
 
+/*
+ * Synthesis for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a library service).  Same arguments, layouts and
+ * stream ordering as sht_alm2map, but the call allocates nothing: its
+ * scratch (the Delta intermediate plus the ring-FFT buffers) is a 64 MiB
+ * static device array, sht_noalloc_scratch_bytes(), that every GPU loading
+ * this library holds until the process exits.  Calls whose scratch
+ * (16 nmaps nrings (mmax+1) bytes, rounded up to 256, plus one ring-FFT
+ * buffer of 48 * max ring length bytes) exceeds it return SHT_EINVAL with
+ * the sizes in sht_plan_last_error.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other threads, other plans)
+ * race; serialise them.  The array keeps the last call's contents; nothing
+ * in it needs to start at zero.
+ */
+sht_status sht_alm2map_noalloc(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream);
+size_t     sht_noalloc_scratch_bytes(void);
+
 const char *sht_status_string(sht_status s);
 const char *sht_plan_last_error(sht_plan_t plan);     /* "" when none */
 

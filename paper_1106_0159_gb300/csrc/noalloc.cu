@@ -1,0 +1,92 @@
+// Synthesis without any device allocation.
+//
+// Some callers cannot call cudaMalloc while they run a transform: code that
+// runs inside another framework's memory pool or under a strict memory
+// budget, or a caller that must not trigger the implicit device
+// synchronisation a cudaMalloc/cudaFree may cause.  For them
+// sht_alm2map_noalloc takes its scratch (the Delta intermediate and the
+// ring-FFT buffers) from one file-scope __device__ array instead of the
+// plan's workspace.
+//
+// The array is 64 MiB and exists on every GPU on which this library's module
+// is loaded, for the life of the process.  Host code may not pass the
+// array's symbol to a kernel (on the host it only names a stand-in object);
+// its device address is looked up with cudaGetSymbolAddress once per device,
+// on the first call made with that device current, and cached.
+#include "sht_internal.h"
+
+#include <mutex>
+#include <string>
+
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+cudaError_t scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" size_t sht_noalloc_scratch_bytes(void) { return NOALLOC_SCRATCH_BYTES; }
+
+extern "C" sht_status sht_alm2map_noalloc(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream)
+{
+    if (!plan || nmaps < 0) return SHT_EINVAL;
+    if (nmaps == 0) return SHT_OK;
+    if (!alm || !map || alm == (const void *)map) return SHT_EINVAL;
+    sht::Plan &p = plan->p;
+    const size_t delta = ((size_t)nmaps * p.nrings * (p.mmax + 1) * sizeof(double2) + 255) & ~(size_t)255;
+    const size_t per_cta = (size_t)3 * p.fft_maxlen * sizeof(double2);
+    if (delta + per_cta > NOALLOC_SCRATCH_BYTES) {
+        p.last_error = "sht_alm2map_noalloc: " + std::to_string(nmaps) + " map(s) need " +
+                       std::to_string(delta + per_cta) + " bytes of scratch; the static scratch holds " +
+                       std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes";
+        return SHT_EINVAL;
+    }
+    int grid = sht::ring_grid(p);
+    const size_t fit = (NOALLOC_SCRATCH_BYTES - delta) / per_cta;
+    if ((size_t)grid > fit) grid = (int)fit;
+    void *base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) {
+        p.last_error = std::string("sht_alm2map_noalloc: scratch address: ") + cudaGetErrorString(e);
+        return SHT_ECUDA;
+    }
+    // Every Delta entry and every FFT buffer entry is written before it is read,
+    // so nothing here needs clearing between calls.
+    double2 *d = (double2 *)base;
+    double2 *scratch = (double2 *)((char *)base + delta);
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = 0;
+    e = sht::launch_legendre_synth(p, (const double2 *)alm, d, nmaps, s, &n);
+    p.launches[0] += n;
+    if (e == cudaSuccess) {
+        e = sht::launch_ring_synth_grid(p, d, map, scratch, nmaps, grid, s);
+        p.launches[1] += 1;
+    }
+    if (e != cudaSuccess) {
+        p.last_error = std::string("sht_alm2map_noalloc: ") + cudaGetErrorString(e);
+        return SHT_ECUDA;
+    }
+    return SHT_OK;
+}

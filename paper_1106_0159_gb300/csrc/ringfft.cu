@@ -392,6 +392,31 @@ cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, 
     return cudaGetLastError();
 }
 
+// Same as launch_ring_synth with a caller-chosen persistent grid (the scratch
+// holds 3 * fft_maxlen complex entries per CTA).
+cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
+                                   int grid, cudaStream_t st)
+{
+    RingArgs A{};
+    A.items = p.d_items;
+    A.lens = p.d_lens;
+    A.tab = p.d_fft_tab;
+    A.phase = p.d_phase;
+    A.ofs = p.d_ofs;
+    A.w = p.d_w;
+    A.scratch = scratch;
+    A.maxlen = p.fft_maxlen;
+    A.nitems = p.nitems;
+    A.nmaps = nmaps;
+    A.nrings = p.nrings;
+    A.mmax = p.mmax;
+    A.npix = p.npix;
+    A.delta_in = delta;
+    A.map_out = map;
+    ring_synth_kernel<<<grid, FFT_T, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ring_anal(const Plan &p, const double *map, double2 *delta, double2 *scratch, int nmaps,
                              cudaStream_t st)
 {

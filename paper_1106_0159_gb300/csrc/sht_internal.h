@@ -106,4 +106,12 @@ int ring_grid(const Plan &p);
 cudaError_t build_phase_table(Plan &p);
 cudaError_t build_fft_tables(Plan &p);
 
+cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
+                                   int grid, cudaStream_t st);
+
 }  // namespace sht
+
+// the opaque handle of the C ABI
+struct sht_plan_s {
+    sht::Plan p;
+};

@@ -11,10 +11,6 @@
 
 using sht::Plan;
 
-struct sht_plan_s {
-    Plan p;
-};
-
 namespace {
 
 const double PI = 3.14159265358979323846;

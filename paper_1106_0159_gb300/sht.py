@@ -33,7 +33,7 @@ EXPORTS = (
     "sht_nalm", "sht_alm_index", "sht_plan_npix", "sht_plan_nrings", "sht_plan_npairs",
     "sht_workspace_bytes", "sht_geom_healpix", "sht_geom_gauss_legendre",
     "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
-    "sht_fp64_fma_tflops",
+    "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
 )
 STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
 
@@ -81,6 +81,8 @@ def load():
             "sht_plan_set_stage_timing": (I, [P, I]),
             "sht_plan_stage_times": (I, [P, P, P, I]),
             "sht_fp64_fma_tflops": (I, [P]),
+            "sht_alm2map_noalloc": (I, [P, P, P, I, P]),
+            "sht_noalloc_scratch_bytes": (S, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -245,6 +247,16 @@ class Plan:
         a = self._dev(alm, torch.complex128, (self.nalm,), "alm")
         o = self._out(out, (a.shape[0], self.npix), torch.float64, a)
         self._run(load().sht_alm2map, a, o, a.shape[0], stream)
+        return o
+
+    def alm2map_noalloc(self, alm, out=None, stream=None):
+        """Synthesis through sht_alm2map_noalloc: the library call itself allocates no device
+        memory (its scratch is a static device array); only `out`, if not given, is allocated
+        here by PyTorch before the call."""
+        import torch
+        a = self._dev(alm, torch.complex128, (self.nalm,), "alm")
+        o = self._out(out, (a.shape[0], self.npix), torch.float64, a)
+        self._run(load().sht_alm2map_noalloc, a, o, a.shape[0], stream)
         return o
 
     def map2alm(self, m, out=None, stream=None):
