@@ -77,6 +77,29 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings,
                            const int64_t *nphi, const double *theta, const double *phi0,
                            const double *w, int lmax, int mmax);
 
+/*
+ * Arithmetic of the Legendre synthesis (the analysis is FP64 in both modes):
+ *   SHT_MODE_FP64        (default) every step in FP64.
+ *   SHT_MODE_SPLIT_BF16  the lambda recurrence in FP64, the sum over l of eq. (matrix_vec) on the
+ *                        tensor cores: both operands cut into six balanced 7-bit digits, digit
+ *                        products accumulated exactly in FP32, combined in FP64.  Relative error
+ *                        against the exact transform <= 1e-9 of the output RMS.  Processes up to
+ *                        16 maps per pass over the recurrence.
+ * Switching to SHT_MODE_SPLIT_BF16 the first time runs one FP64 pass of the recurrence to
+ * measure the scale of its values per (m, block of 128 ring slots) (synchronous; about the cost
+ * of one single-map synthesis).  SHT_EINVAL for an unknown mode.
+ */
+typedef enum { SHT_MODE_FP64 = 0, SHT_MODE_SPLIT_BF16 = 1 } sht_mode;
+sht_status sht_plan_set_mode(sht_plan_t plan, int mode);
+int        sht_plan_mode(sht_plan_t plan);
+
+/*
+ * Device status word of the plan: bit 0 is set when a bounded wait inside a tensor-core kernel
+ * gave up (the kernel then wrote no output for that block and released its resources).
+ * Copies the word to *status (synchronous); clear != 0 resets it.
+ */
+sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear);
+
 /* Free the plan, its device tables and workspace (synchronises the device). NULL is ignored. */
 void sht_plan_destroy(sht_plan_t plan);
 

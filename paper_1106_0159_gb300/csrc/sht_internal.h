@@ -68,6 +68,15 @@ struct Plan {
     int64_t fft_tab_len = 0;
     int fft_maxlen = 0;         // per-CTA scratch length (complex entries, per buffer)
 
+    // precision form (split-bf16 contraction on the tensor cores)
+    int mode = 0;                       // SHT_MODE_FP64 or SHT_MODE_SPLIT_BF16
+    int64_t tc_total_chunks = 0;        // sum over m of ceil((lmax - m + 1) / 32)
+    int64_t *d_tc_chunk_base = nullptr; // [mmax + 1]
+    int *d_tc_chunk_m = nullptr;        // [tc_total_chunks]
+    int *d_tc_Ey = nullptr;             // [mmax + 1][slot blocks] scale exponent of y = lambda / c
+    int *d_status = nullptr;            // device status word (bounded waits that gave up)
+    bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
+
     // workspace, grown on demand
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -105,6 +114,13 @@ int ring_grid(const Plan &p);
 // plan-time table builders (ringfft.cu); synchronous on the legacy stream
 cudaError_t build_phase_table(Plan &p);
 cudaError_t build_fft_tables(Plan &p);
+
+size_t tc_workspace_bytes(const Plan &p, int nmaps);
+cudaError_t build_tc_scales(Plan &p);
+cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,
+                                     cudaStream_t st, int *nlaunch);
+cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
+                                        int *nlaunch);
 
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st);

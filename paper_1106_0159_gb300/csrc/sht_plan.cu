@@ -26,7 +26,8 @@ sht_status cuda_fail(Plan &p, cudaError_t e, const char *where)
 void free_plan_device(Plan &p)
 {
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
-                    p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws};
+                    p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
+                    p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -39,6 +40,10 @@ void free_plan_device(Plan &p)
     p.d_fft_tab = nullptr;
     p.d_rein = nullptr;
     p.d_ws = nullptr;
+    p.d_tc_chunk_base = nullptr;
+    p.d_tc_chunk_m = nullptr;
+    p.d_tc_Ey = nullptr;
+    p.d_status = nullptr;
     p.ws_bytes = 0;
 }
 
@@ -249,15 +254,32 @@ struct StageScope {
     }
 };
 
-sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t s)
+// tc_scratch: tc_workspace_bytes(p, min(nmaps, 16)) bytes, used in the precision form only
+sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, void *tc_scratch, int nmaps,
+                              cudaStream_t s)
 {
     StageScope sc(p, 0, s);
     int n = 0;
-    cudaError_t e = sht::launch_legendre_synth(p, alm, delta, nmaps, s, &n);
-    p.launches[0] += n;
+    cudaError_t e;
+    if (p.mode == SHT_MODE_SPLIT_BF16) {
+        e = sht::launch_legendre_synth_polar(p, alm, delta, nmaps, s, &n);
+        p.launches[0] += n;
+        if (e == cudaSuccess) {
+            e = sht::launch_legendre_synth_tc(p, alm, delta, tc_scratch, nmaps, s, &n);
+            p.launches[0] += n;
+        }
+    } else {
+        e = sht::launch_legendre_synth(p, alm, delta, nmaps, s, &n);
+        p.launches[0] += n;
+    }
     if (e != cudaSuccess) return cuda_fail(p, e, "legendre_synth");
     sc.done();
     return SHT_OK;
+}
+
+size_t synth_scratch_bytes(const Plan &p, int nmaps)
+{
+    return p.mode == SHT_MODE_SPLIT_BF16 ? sht::tc_workspace_bytes(p, std::min(nmaps, 16)) : 0;
 }
 
 sht_status run_ring_synth(Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps, cudaStream_t s)
@@ -341,7 +363,32 @@ size_t sht_workspace_bytes(sht_plan_t plan, int nmaps)
     const size_t d = align256(delta_bytes(p, nmaps));
     const size_t r = align256(sht::ring_scratch_bytes(p));
     const size_t a = align256(sht::legendre_anal_partial_bytes(p, nmaps));
-    return d + std::max(r, a);
+    const size_t t = align256(synth_scratch_bytes(p, nmaps));
+    return d + std::max(std::max(r, a), t);
+}
+
+sht_status sht_plan_set_mode(sht_plan_t plan, int mode)
+{
+    if (!plan || (mode != SHT_MODE_FP64 && mode != SHT_MODE_SPLIT_BF16)) return SHT_EINVAL;
+    Plan &p = plan->p;
+    if (mode == SHT_MODE_SPLIT_BF16) {
+        cudaError_t e = sht::build_tc_scales(p);  // one FP64 pass of the recurrence, synchronous
+        if (e != cudaSuccess) return cuda_fail(p, e, "precision-form scales");
+    }
+    p.mode = mode;
+    return SHT_OK;
+}
+
+int sht_plan_mode(sht_plan_t plan) { return plan ? plan->p.mode : -1; }
+
+sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
+{
+    if (!plan || !status) return SHT_EINVAL;
+    Plan &p = plan->p;
+    cudaError_t e = cudaMemcpy(status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(p.d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(p, e, "device status");
+    return SHT_OK;
 }
 
 sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int64_t *nphi, const double *theta,
@@ -390,6 +437,18 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     p.mR = any_polar ? std::min(mmax, lmax / 10 + 64) : -1;
     std::vector<double3> rein;
     reinsch_tables(lmax, p.mR, rein);
+    p.polar_first_slot = p.mR >= 0 && s[0] < 0.03;
+    // precision form: 32-l chunks per m
+    std::vector<int64_t> chunk_base(mmax + 1);
+    int64_t nchunks = 0;
+    for (int m = 0; m <= mmax; ++m) {
+        chunk_base[m] = nchunks;
+        nchunks += (lmax - m + 32) / 32;
+    }
+    p.tc_total_chunks = nchunks;
+    std::vector<int> chunk_m(nchunks);
+    for (int m = 0; m <= mmax; ++m)
+        for (int64_t c = chunk_base[m]; c < (m < mmax ? chunk_base[m + 1] : nchunks); ++c) chunk_m[c] = m;
     std::vector<int> nphi32(nrings);
     for (int r = 0; r < nrings; ++r) nphi32[r] = (int)nphi[r];
 
@@ -402,6 +461,12 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     if (e == cudaSuccess) e = upload(&p.d_alpha, alpha.data(), alpha.size());
     if (e == cudaSuccess) e = upload(&p.d_cfac, cfac.data(), cfac.size());
     if (e == cudaSuccess && p.mR >= 0) e = upload(&p.d_rein, rein.data(), rein.size());
+    if (e == cudaSuccess) e = upload(&p.d_tc_chunk_base, chunk_base.data(), chunk_base.size());
+    if (e == cudaSuccess) e = upload(&p.d_tc_chunk_m, chunk_m.data(), chunk_m.size());
+    if (e == cudaSuccess) {
+        const int zero = 0;
+        e = upload(&p.d_status, &zero, 1);
+    }
     if (e == cudaSuccess) e = upload(&p.d_ofs, p.ofs.data(), p.ofs.size());
     if (e == cudaSuccess) e = upload(&p.d_nphi, nphi32.data(), nphi32.size());
     if (e == cudaSuccess) e = upload(&p.d_w, p.w.data(), p.w.size());
@@ -444,7 +509,9 @@ sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int
     sht_status st = check_call(plan, alm, delta, nmaps);
     if (st != SHT_OK || nmaps == 0) return st;
     Plan &p = plan->p;
-    return run_legendre_synth(p, (const double2 *)alm, (double2 *)delta, nmaps, (cudaStream_t)stream);
+    st = ensure_workspace(p, align256(synth_scratch_bytes(p, nmaps)));
+    if (st != SHT_OK) return st;
+    return run_legendre_synth(p, (const double2 *)alm, (double2 *)delta, p.d_ws, nmaps, (cudaStream_t)stream);
 }
 
 sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int nmaps, void *stream)
@@ -484,12 +551,12 @@ sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps,
     if (st != SHT_OK || nmaps == 0) return st;
     Plan &p = plan->p;
     const size_t d = align256(delta_bytes(p, nmaps));
-    st = ensure_workspace(p, d + align256(sht::ring_scratch_bytes(p)));
+    st = ensure_workspace(p, d + std::max(align256(sht::ring_scratch_bytes(p)), align256(synth_scratch_bytes(p, nmaps))));
     if (st != SHT_OK) return st;
     double2 *delta = (double2 *)p.d_ws;
     double2 *scratch = (double2 *)((char *)p.d_ws + d);
     cudaStream_t s = (cudaStream_t)stream;
-    st = run_legendre_synth(p, (const double2 *)alm, delta, nmaps, s);
+    st = run_legendre_synth(p, (const double2 *)alm, delta, scratch, nmaps, s);
     if (st != SHT_OK) return st;
     return run_ring_synth(p, delta, map, scratch, nmaps, s);
 }

@@ -34,7 +34,9 @@ EXPORTS = (
     "sht_workspace_bytes", "sht_geom_healpix", "sht_geom_gauss_legendre",
     "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
+    "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status",
 )
+MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
 
 
@@ -83,6 +85,9 @@ def load():
             "sht_fp64_fma_tflops": (I, [P]),
             "sht_alm2map_noalloc": (I, [P, P, P, I, P]),
             "sht_noalloc_scratch_bytes": (S, []),
+            "sht_plan_set_mode": (I, [P, I]),
+            "sht_plan_mode": (I, [P]),
+            "sht_plan_device_status": (I, [P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -197,6 +202,19 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_mode(self, mode: int):
+        """MODE_FP64 (default) or MODE_SPLIT_BF16 (tensor-core contraction in the synthesis)."""
+        _check(load().sht_plan_set_mode(self._h, int(mode)), self._h, "sht_plan_set_mode")
+
+    @property
+    def mode(self) -> int:
+        return int(load().sht_plan_mode(self._h))
+
+    def device_status(self, clear: bool = True) -> int:
+        v = ctypes.c_int()
+        _check(load().sht_plan_device_status(self._h, ctypes.byref(v), 1 if clear else 0), self._h)
+        return int(v.value)
 
     def set_stage_timing(self, enable: bool):
         _check(load().sht_plan_set_stage_timing(self._h, 1 if enable else 0), self._h)
