@@ -1,0 +1,363 @@
+// Precision form of the Legendre analysis (eq. almdef, Algorithm 5): the
+// lambda recurrence stays in FP64; the products lambda * Delta^S and their
+// sum over ring slots run on the FP32 pipe in double-float arithmetic.
+//
+// On this part FP32 issues 64 times faster than FP64 (2 FP64 FMA per SM per
+// cycle).  A value v (FP64) is carried as hi + lo, two floats holding 48 bits
+// of its 53-bit significand: hi the leading 24 bits (truncated), lo the next
+// 24 of the remainder, both cut from the bit pattern with integer operations
+// (an FP64 -> FP32 conversion would take an FP64 issue slot).  A product is
+// formed exactly to ~2^-46 with FMA (ph = yh*xh, pl = fma(yh, xh, -ph) +
+// yh*xl + yl*xh) and sums use TwoSum on the hi parts, so partial sums keep
+// about 2^-44 relative accuracy, far inside the 1e-9 bar of this form.
+//
+// CTA: one m, 256 ring slots (one per thread, 8 warps).  Sigma = D_N + D_S
+// and D = D_N - D_S for up to 16 maps (32 real columns) sit in shared memory
+// as double-float pairs.  Per group of 8 l, every lane forms its 8 products
+// per column and a warp reduce-scatter (TwoSum) leaves each lane the warp
+// total of one l; the eight warps' totals are added in shared memory and the
+// block's partial a_lm (times 1/c, as in the FP64 kernel) is written as a
+// double-float pair per component.  The fixed-order block reduction then
+// converts and sums the blocks in FP64.
+//
+// Polar slot blocks run the Reinsch form in the FP64 kernel (see legendre.cu);
+// here the first block of a polar plan is skipped for m <= mR and covered by
+// launch_legendre_anal_polar.
+#include "sht_internal.h"
+
+#include <algorithm>
+
+namespace sht {
+namespace {
+
+constexpr int DF_T = 256;          // threads = slots per CTA
+constexpr int DF_CHL = 32;         // l per shared-memory chunk (multiple of 8)
+constexpr int DF_G = 8;            // l per reduce-scatter round
+constexpr int RESCALE_THR = 1023 + 256;
+constexpr double POLAR_SIN = 0.03;  // must match legendre.cu
+
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+__device__ __forceinline__ void normalise(double &v, int &e)
+{
+    int hi = __double2hiint(v);
+    e += ((hi >> 20) & 0x7ff) - 1023;
+    hi = (hi & 0x800fffff) | (1023 << 20);
+    v = __hiloint2double(hi, __double2loint(v));
+}
+
+__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+
+__device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
+{
+    if (m > 0 && !(s > 1e-300)) {
+        y0 = 0.0;
+        k = 0;
+        return;
+    }
+    double r = 1.0;
+    int er = 0;
+    double b = s;
+    int eb = 0;
+    if (m > 0) normalise(b, eb);
+    for (int mm = m; mm; mm >>= 1) {
+        if (mm & 1) {
+            r *= b;
+            er += eb;
+            normalise(r, er);
+        }
+        if (mm > 1) {
+            b *= b;
+            eb *= 2;
+            normalise(b, eb);
+        }
+    }
+    int kk = (er >= 0) ? 0 : -((-er) >> 9);
+    int rem = er - 512 * kk;
+    y0 = mu * r * pow2i(rem);
+    k = kk;
+}
+
+// v -> hi + lo from the bit pattern (integer pipe).  Values below 2^-126 flush to zero
+// (their share of any sum here is below 2^-100 of the largest term).
+__device__ __forceinline__ float2 d2df(double v)
+{
+    const int hiw = __double2hiint(v);
+    const unsigned low = (unsigned)__double2loint(v);
+    const int ex = (hiw >> 20) & 0x7ff;
+    const int e = ex - 1023;
+    if (ex == 0 || e < -126) return make_float2(0.f, 0.f);
+    const unsigned sign = (unsigned)hiw & 0x80000000u;
+    // hi: sign, exponent, top 23 fraction bits (20 from the high word, 3 from the low word)
+    const unsigned frac23 = (((unsigned)hiw & 0xFFFFFu) << 3) | (low >> 29);
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | frac23);
+    // lo: the remaining 29 fraction bits times 2^(e - 52), rounded to 24 bits (zero when
+    // 2^(e - 52) is below the normal float range; hi alone then carries 24 bits)
+    const unsigned rem = low & 0x1FFFFFFFu;
+    const float sc = (e - 52 >= -126) ? __uint_as_float((unsigned)(e - 52 + 127) << 23) : 0.f;
+    const float lo = (float)rem * sc;
+    return make_float2(hi, sign ? -lo : lo);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 y, float2 x)
+{
+    const float ph = y.x * x.x;
+    float pl = fmaf(y.x, x.x, -ph);
+    pl = fmaf(y.x, x.y, pl);
+    pl = fmaf(y.y, x.x, pl);
+    return make_float2(ph, pl);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float err = (a.x - (s - bb)) + (b.x - bb);
+    return make_float2(s, err + a.y + b.y);
+}
+
+__device__ __forceinline__ float2 shfl_xor_df(float2 v, int m)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Reduce-scatter of DF_G double-float values per lane over the warp: every lane ends with the
+// warp total of value (lane & (DF_G - 1)).
+__device__ __forceinline__ float2 warp_reduce_scatter_df(float2 v[DF_G])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = DF_G / 2; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float2 send = up ? v[i] : v[i + h];
+            const float2 keep = up ? v[i + h] : v[i];
+            v[i] = df_add(keep, shfl_xor_df(send, h));
+        }
+    }
+    float2 r = v[0];
+    r = df_add(r, shfl_xor_df(r, 8));
+    r = df_add(r, shfl_xor_df(r, 16));
+    return r;
+}
+
+struct DfArgs {
+    const double2 *delta;  // [nmaps][nrings][mmax+1], first map of this group
+    float4 *partial;       // [nblk][nmaps_total][nalm] as (re_hi, re_lo, im_hi, im_lo)
+    const int *slotN, *slotS;
+    const double *u, *s;
+    const double *alpha, *cfac;
+    int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
+    int64_t nalm;
+    int64_t part_blk_stride;  // nmaps_total * nalm
+};
+
+template <int N>
+struct DfSmem {
+    float2 X[2][N][DF_T];           // [parity: Sigma, D][column][slot]
+    float2 red[DF_T / 32][DF_CHL][N];
+    double al[DF_CHL];
+};
+
+template <int N>
+__global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DfSmem<N> &S = *reinterpret_cast<DfSmem<N> *>(smem_raw);
+    constexpr int NW = DF_T / 32;
+    const int m = blockIdx.x / A.nblk;
+    const int blk = blockIdx.x - m * A.nblk;
+    if (m <= A.mR && A.s[blk * DF_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int slot = blk * DF_T + tid;
+    const bool active = slot < A.nslots;
+    const int L = A.lmax;
+    const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
+    const int64_t mstride = A.mmax + 1;
+
+    double u = 0.0, y1 = 0.0, y2 = 0.0;
+    int k = 0;
+    if (active) {
+        u = A.u[slot];
+        double y0;
+        sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
+        y2 = -y0;
+    }
+    // Sigma and D of this slot, as double-float columns (2g: re, 2g+1: im)
+    {
+        const int rn = active ? A.slotN[slot] : -1, rs = active ? A.slotS[slot] : -1;
+#pragma unroll
+        for (int g = 0; g < N / 2; ++g) {
+            double2 dn = make_double2(0.0, 0.0), ds = make_double2(0.0, 0.0);
+            if (g < A.nmaps) {
+                const double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+                if (rn >= 0) dn = d[(int64_t)rn * mstride + m];
+                if (rs >= 0) ds = d[(int64_t)rs * mstride + m];
+            }
+            S.X[0][2 * g][tid] = d2df(dn.x + ds.x);
+            S.X[0][2 * g + 1][tid] = d2df(dn.y + ds.y);
+            S.X[1][2 * g][tid] = d2df(dn.x - ds.x);
+            S.X[1][2 * g + 1][tid] = d2df(dn.y - ds.y);
+        }
+    }
+
+    for (int l0 = m; l0 <= L; l0 += DF_CHL) {
+        const int nl = min(DF_CHL, L - l0 + 1);
+        __syncthreads();
+        if (tid < DF_CHL) S.al[tid] = (tid < nl) ? A.alpha[base + (l0 - m) + tid] : 0.0;
+        __syncthreads();
+        for (int j0 = 0; j0 < DF_CHL; j0 += DF_G) {
+            // 8 recurrence steps (past the end: no-op steps with zero values)
+            const bool scaled = __any_sync(0xffffffffu, k < 0);
+            float2 yv[DF_G];
+            bool live = false;
+#pragma unroll
+            for (int jj = 0; jj < DF_G; ++jj) {
+                const int j = j0 + jj;
+                double y = 0.0;
+                if (j < nl) {
+                    const double t = fma(-u, y1, y1);
+                    y = fma(S.al[j], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+                }
+                const bool use = active && j < nl && !(scaled && k < 0);
+                yv[jj] = use ? d2df(y) : make_float2(0.f, 0.f);
+                live |= use;
+            }
+            if (((j0 + 8) & 15) == 0 && scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                y1 *= 0x1p-512;
+                y2 *= 0x1p-512;
+                k += 1;
+            }
+            if (!__any_sync(0xffffffffu, live)) {
+                if (lane < DF_G) {
+#pragma unroll
+                    for (int n = 0; n < N; ++n) S.red[warp][j0 + lane][n] = make_float2(0.f, 0.f);
+                }
+                continue;
+            }
+#pragma unroll 4
+            for (int n = 0; n < N; ++n) {
+                const float2 xe = S.X[0][n][tid], xo = S.X[1][n][tid];
+                float2 p[DF_G];
+#pragma unroll
+                for (int jj = 0; jj < DF_G; ++jj) p[jj] = df_mul(yv[jj], (jj & 1) ? xo : xe);  // l - m parity = jj's
+                const float2 r = warp_reduce_scatter_df(p);
+                if (lane < DF_G) S.red[warp][j0 + lane][n] = r;
+            }
+        }
+        __syncthreads();
+        // add the warps, divide by c (the block reduction multiplies by it), write the block's partial
+        for (int i = tid; i < nl * (N / 2); i += DF_T) {
+            const int j = i % nl, g = i / nl;
+            float2 re = S.red[0][j][2 * g], im = S.red[0][j][2 * g + 1];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) {
+                re = df_add(re, S.red[w][j][2 * g]);
+                im = df_add(im, S.red[w][j][2 * g + 1]);
+            }
+            if (g < A.nmaps) {
+                A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.nalm + base + (l0 - m) + j] =
+                    make_float4(re.x, re.y, im.x, im.y);
+            }
+        }
+    }
+}
+
+// a_lm = c_lm * sum over blocks of (hi + lo) in FP64.  Block 0 holds FP64 partials (double2,
+// from the Reinsch kernel) for the indices below fp64_lim, i.e. for m <= mR of a polar plan.
+__global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double *__restrict__ cfac,
+                                        double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
+                                        int64_t blk_stride, int64_t fp64_lim)
+{
+    const int64_t total = nalm * nmaps;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / nalm, i = t - g * nalm;
+        double re = 0.0, im = 0.0;
+        for (int bk = 0; bk < nblk; ++bk) {
+            const float4 v = partial[bk * blk_stride + g * nalm + i];
+            if (bk == 0 && i < fp64_lim) {
+                const double2 d = *reinterpret_cast<const double2 *>(&v);
+                re += d.x;
+                im += d.y;
+            } else {
+                re += (double)v.x + (double)v.y;
+                im += (double)v.z + (double)v.w;
+            }
+        }
+        const double c = cfac[i];
+        alm[t] = make_double2(c * re, i <= lmax ? 0.0 : c * im);
+    }
+}
+
+template <int N>
+cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
+{
+    const int smem = (int)sizeof(DfSmem<N>);
+    cudaError_t e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    legendre_anal_df_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), DF_T, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int legendre_anal_df_nblk(const Plan &p) { return (p.nslots + DF_T - 1) / DF_T; }
+
+size_t legendre_anal_df_partial_bytes(const Plan &p, int nmaps)
+{
+    return (size_t)legendre_anal_df_nblk(p) * (size_t)nmaps * (size_t)p.nalm * sizeof(float4);
+}
+
+// The precision-form analysis: double-float CTAs for every non-polar slot block, the FP64
+// Reinsch kernel for block 0 when it is polar (m <= mR), then the block reduction.
+cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
+                                    cudaStream_t st, int *nlaunch)
+{
+    *nlaunch = 0;
+    DfArgs A{};
+    A.slotN = p.d_slotN;
+    A.slotS = p.d_slotS;
+    A.u = p.d_u;
+    A.s = p.d_s;
+    A.alpha = p.d_alpha;
+    A.cfac = p.d_cfac;
+    A.nslots = p.nslots;
+    A.nblk = legendre_anal_df_nblk(p);
+    A.lmax = p.lmax;
+    A.mmax = p.mmax;
+    A.nrings = p.nrings;
+    A.mR = p.polar_first_slot ? p.mR : -1;
+    A.nalm = p.nalm;
+    A.part_blk_stride = (int64_t)nmaps * p.nalm;
+    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    int g0 = 0;
+    while (g0 < nmaps) {
+        const int nm = std::min(16, nmaps - g0);
+        A.nmaps = nm;
+        A.delta = delta + (int64_t)g0 * dstride;
+        A.partial = (float4 *)partial + (int64_t)g0 * p.nalm;
+        cudaError_t e = nm > 8 ? launch_df_group<32>(p, A, st) : launch_df_group<16>(p, A, st);
+        ++*nlaunch;
+        if (e != cudaSuccess) return e;
+        g0 += nm;
+    }
+    int64_t fp64_lim = 0;
+    if (A.mR >= 0) {
+        int n = 0;
+        cudaError_t e = launch_legendre_anal_polar(p, delta, (double2 *)partial, nmaps, DF_T, st, &n);
+        *nlaunch += n;
+        if (e != cudaSuccess) return e;
+        fp64_lim = (int64_t)(A.mR + 1) * (2 * (int64_t)p.lmax + 3 - (A.mR + 1)) / 2;  // index(mR+1, mR+1)
+    }
+    const int64_t total = p.nalm * nmaps;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>((const float4 *)partial, p.d_cfac, alm, A.nblk, p.nalm, nmaps,
+                                                   p.lmax, A.part_blk_stride, fp64_lim);
+    ++*nlaunch;
+    return cudaGetLastError();
+}
+
+}  // namespace sht

@@ -115,6 +115,12 @@ int ring_grid(const Plan &p);
 cudaError_t build_phase_table(Plan &p);
 cudaError_t build_fft_tables(Plan &p);
 
+cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, double2 *partial, int nmaps, int slots,
+                                       cudaStream_t st, int *nlaunch);
+int legendre_anal_df_nblk(const Plan &p);
+size_t legendre_anal_df_partial_bytes(const Plan &p, int nmaps);
+cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
+                                    cudaStream_t st, int *nlaunch);
 size_t tc_workspace_bytes(const Plan &p, int nmaps);
 cudaError_t build_tc_scales(Plan &p);
 cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,

@@ -282,6 +282,12 @@ size_t synth_scratch_bytes(const Plan &p, int nmaps)
     return p.mode == SHT_MODE_SPLIT_BF16 ? sht::tc_workspace_bytes(p, std::min(nmaps, 16)) : 0;
 }
 
+size_t anal_partial_bytes(const Plan &p, int nmaps)
+{
+    return p.mode == SHT_MODE_SPLIT_BF16 ? sht::legendre_anal_df_partial_bytes(p, nmaps)
+                                         : sht::legendre_anal_partial_bytes(p, nmaps);
+}
+
 sht_status run_ring_synth(Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps, cudaStream_t s)
 {
     StageScope sc(p, 1, s);
@@ -305,6 +311,16 @@ sht_status run_ring_anal(Plan &p, const double *map, double2 *delta, double2 *sc
 sht_status run_legendre_anal(Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
                              cudaStream_t s)
 {
+    if (p.mode == SHT_MODE_SPLIT_BF16) {
+        // precision form: double-float products and slot sums on the FP32 pipe (reduction included)
+        StageScope sc(p, 3, s);
+        int n = 0;
+        cudaError_t e = sht::launch_legendre_anal_df(p, delta, alm, partial, nmaps, s, &n);
+        p.launches[3] += n;
+        if (e != cudaSuccess) return cuda_fail(p, e, "legendre_anal");
+        sc.done();
+        return SHT_OK;
+    }
     {
         StageScope sc(p, 3, s);
         int n = 0;
@@ -362,7 +378,7 @@ size_t sht_workspace_bytes(sht_plan_t plan, int nmaps)
     const Plan &p = plan->p;
     const size_t d = align256(delta_bytes(p, nmaps));
     const size_t r = align256(sht::ring_scratch_bytes(p));
-    const size_t a = align256(sht::legendre_anal_partial_bytes(p, nmaps));
+    const size_t a = align256(anal_partial_bytes(p, nmaps));
     const size_t t = align256(synth_scratch_bytes(p, nmaps));
     return d + std::max(std::max(r, a), t);
 }
@@ -539,7 +555,7 @@ sht_status sht_legendre_anal(sht_plan_t plan, const void *delta, void *alm, int 
     sht_status st = check_call(plan, delta, alm, nmaps);
     if (st != SHT_OK || nmaps == 0) return st;
     Plan &p = plan->p;
-    st = ensure_workspace(p, align256(sht::legendre_anal_partial_bytes(p, nmaps)));
+    st = ensure_workspace(p, align256(anal_partial_bytes(p, nmaps)));
     if (st != SHT_OK) return st;
     return run_legendre_anal(p, (const double2 *)delta, (double2 *)alm, (double2 *)p.d_ws, nmaps,
                              (cudaStream_t)stream);
@@ -568,7 +584,7 @@ sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps,
     Plan &p = plan->p;
     const size_t d = align256(delta_bytes(p, nmaps));
     const size_t r = align256(sht::ring_scratch_bytes(p));
-    const size_t a = align256(sht::legendre_anal_partial_bytes(p, nmaps));
+    const size_t a = align256(anal_partial_bytes(p, nmaps));
     st = ensure_workspace(p, d + std::max(r, a));
     if (st != SHT_OK) return st;
     double2 *delta = (double2 *)p.d_ws;

@@ -101,3 +101,46 @@ def test_split_bf16_full_size_sampled(nside, L, nmaps):
     s64 = host(q.alm2map(dev(a[:2])))
     for g in range(2):
         assert rel(s[g], s64[g]) < TOL_TC
+
+
+# ---------------------------------------------------------------- analysis in the precision form
+# (double-float products and slot sums on the FP32 pipe; the recurrence in FP64)
+
+@pytest.mark.parametrize("nside,L,nmaps", [(32, 64, 1), (64, 128, 5), (128, 256, 16), (128, 256, 19)])
+def test_split_analysis_against_oracle(nside, L, nmaps):
+    geom = geometry.healpix(nside)
+    p = _plan(geom, L)
+    s = inputs.white_map(geometry.npix(geom), seed=70 + nmaps, nmaps=nmaps)
+    b = host(p.map2alm(dev(s)))
+    l, m = inputs.lm_arrays(L, L)
+    for g in sorted({0, nmaps - 1}):
+        ref = oracle.map2alm_rings(geom, s[g], L, L)
+        assert rel(b[g], ref) < TOL_TC, g
+        assert np.all(b[g][m == 0].imag == 0)
+
+
+def test_split_analysis_matches_fp64_path_and_round_trip():
+    L = 256
+    geom = geometry.gauss_legendre(L + 1, 2 * L + 1)
+    a = inputs.uniform_alm(L, L, seed=71, nmaps=3)
+    p = _plan(geom, L)
+    q = _plain(geom, L)
+    s = p.alm2map(dev(a))
+    b = host(p.map2alm(s))
+    b64 = host(q.map2alm(s))
+    for g in range(3):
+        assert rel(b[g], b64[g]) < 1e-12   # double-float keeps ~2^-44
+        assert rel(b[g], a[g]) < TOL_TC     # round trip in the precision form
+
+
+@pytest.mark.parametrize("nside,L", [(1024, 2048), (2048, 4096)])
+def test_split_analysis_full_size_sampled(nside, L):
+    geom = geometry.healpix(nside)
+    p = _plan(geom, L)
+    s = inputs.white_map(geometry.npix(geom), seed=72, nmaps=16)
+    b = host(p.map2alm(dev(s)))
+    ms = [0, 1, 3, L // 3, L - 1, L]
+    for g in (0, 15):
+        refs = oracle.map2alm_ms(geom, s[g], L, ms)
+        got = np.concatenate([b[g][oracle.alm_index(L, mm, mm):oracle.alm_index(L, mm, mm) + L - mm + 1] for mm in ms])
+        assert rel(got, np.concatenate(refs)) < TOL_TC
