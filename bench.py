@@ -30,6 +30,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 SM_MAX_MHZ = 2070  # GB300 maximum SM clock
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+MEASURED = _measured_peaks()
 METRIC = "ℓmax=4096 alm2map+map2alm maps/s, served vs plain; p99 ms; % FP64/TC peak"
 DATA = "synthetic: seeded complex Gaussian a_lm with C_l = 1/(l(l+1)+1), a_l0 real (CMB-like)"
 
@@ -45,12 +55,21 @@ def parse():
     ap.add_argument("--maps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="split", choices=["split", "fp64"],
+                    help="split: tensor-core synthesis + double-float analysis (<= 1e-9); fp64: plain")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
     return ap.parse_args()
 
 
-def workload_name(a):
+MODES = {"split": "precision form: FP64 recurrence, tensor-core (tcgen05, split-bf16) synthesis sum, "
+                  "double-float FP32 analysis sum",
+         "fp64": "plain FP64"}
+
+
+def workload_name(a, mode=None):
     return ("alm2map then map2alm round trip, HEALPix Nside=%d (%d px, %d rings), lmax=mmax=%d, "
-            "%d maps per step, plain FP64" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps))
+            "%d maps per step, %s" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps,
+                                       MODES[mode or a.mode]))
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -229,30 +248,87 @@ def ours_arm(a, rank, world, local_rank):
         plan.alm2map(alm, out=mp)
         plan.map2alm(mp, out=alm_out)
 
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize()
-    plan.set_stage_timing(True)
-    plan.stage_times(reset=True)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
-    clocks = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    evs[0].record(stream)
-    for i in range(a.steps):
-        step()
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    stages = plan.stage_times(reset=True)
-    plan.set_stage_timing(False)
-    total_ms = rep.max_over_ranks(total_ms, device="cuda")
+    def timed(mode, steps, warmup, sample_clocks):
+        plan.set_mode(sht.MODE_SPLIT_BF16 if mode == "split" else sht.MODE_FP64)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        plan.set_stage_timing(True)
+        plan.stage_times(reset=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        clocks = ClockSampler(local_rank) if sample_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        evs[0].record(stream)
+        for i in range(steps):
+            step()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        total = rep.max_over_ranks(evs[0].elapsed_time(evs[-1]), device="cuda")
+        stages = plan.stage_times(reset=True)
+        plan.set_stage_timing(False)
+        return {"total_ms": total, "step_ms": step_ms, "stages": stages, "clocks": clk}
+
+    S = sum(L - m + 1 for m in range(L + 1)) * plan.npairs  # (l, m, ring-pair) steps of one transform
+
+    def fp64_roofline(run, steps):
+        # dominant Legendre stage on the FP64 pipe: nominal 3 flops per step for each launch's
+        # recurrence plus 4 flops per step per map for the accumulation
+        legendre = {k: v for k, v in run["stages"].items() if k in ("legendre_synth", "legendre_anal")}
+        dom = max(legendre, key=lambda k: legendre[k][0])
+        dom_ms, dom_launches = legendre[dom]
+        flops = S * (3.0 * dom_launches + 4.0 * B * steps)
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        key = "legendre_anal_kernel" if dom == "legendre_anal" else "legendre_synth_kernel"
+        return {"bound": "alu", "pipe": "fp64", "kernel": key, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic_from_profiles(key),
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe %.3f "
+                               "TF/s" % (nsm, SM_MAX_MHZ, probe_tf),
+                "work": "7 flops per (l, m, ring-pair) step over the full triangle, per map (3 recurrence + 4 "
+                        "accumulate); steps whose lambda is below 2^-224 are skipped, so frac can exceed 1"}
+
+    def split_roofline(run, steps):
+        st = run["stages"]
+        if st["legendre_anal"][0] >= st["legendre_synth"][0]:
+            # double-float analysis on the FP32 pipe: per (l, m, ring-pair, map) two real products
+            # (1 FMUL + 3 FFMA = 7 flops each) and their double-float sums (TwoSum + 2 adds = 8 flops)
+            ms = st["legendre_anal"][0]
+            peak = 2 * 128 * nsm * SM_MAX_MHZ * 1e6 / 1e12
+            achieved = 30.0 * S * B * steps / (ms * 1e-3) / 1e12
+            return {"bound": "alu", "pipe": "fp32", "kernel": "legendre_anal_df_kernel", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": traffic_from_profiles("legendre_anal_df_kernel"),
+                    "peak_source": "derived: 128 FP32 FMA/clk/SM x %d SMs x %d MHz x 2 flop" % (nsm, SM_MAX_MHZ),
+                    "work": "30 FP32 flops per (l, m, ring-pair, map): two double-float real products and sums"}
+        ms = st["legendre_synth"][0]
+        peak = MEASURED.get("bf16_tflops_sustained") or 1725.1
+        achieved = 42.0 * S * 2 * B * steps / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "pipe": "tcgen05 bf16", "kernel": "tc_synth_kernel", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles("tc_synth_kernel"),
+                "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json)",
+                "work": "21 digit products x 2 flops per (l, m, ring-pair, real column)"}
+
+    head = timed(a.mode, a.steps, a.warmup, True)
+    total_ms, step_ms, stages, clk = head["total_ms"], head["step_ms"], head["stages"], head["clocks"]
     value = job_throughput(world, B * a.steps, total_ms)
+    roofline = split_roofline(head, a.steps) if a.mode == "split" else fp64_roofline(head, a.steps)
+    launches = sum(v[1] for v in stages.values())
+
+    plain = None
+    if a.mode == "split" and a.plain_steps > 0:
+        pr = timed("fp64", a.plain_steps, 1, False)
+        plain = {"value": job_throughput(world, B * a.plain_steps, pr["total_ms"]), "unit": "maps/s",
+                 "ms_per_step": pr["total_ms"] / a.plain_steps, "steps": a.plain_steps, "warmup": 1,
+                 "stages_ms_per_step": {k: v[0] / a.plain_steps for k, v in pr["stages"].items()},
+                 "roofline": fp64_roofline(pr, a.plain_steps)}
+        plan.set_mode(sht.MODE_SPLIT_BF16)
 
     # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory
     e2e = None
@@ -280,25 +356,6 @@ def ours_arm(a, rank, world, local_rank):
         e2e = {"value": job_throughput(world, B * a.steps, ems), "unit": "maps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
-    # roofline of the dominant stage (FP64 pipe): nominal 3 flops per (l, m, ring-pair) step for the
-    # recurrence of each launch plus 4 flops per step per map for the accumulation
-    S = sum(L - m + 1 for m in range(L + 1)) * plan.npairs
-    legendre = {k: v for k, v in stages.items() if k in ("legendre_synth", "legendre_anal")}
-    dom = max(legendre, key=lambda k: legendre[k][0])
-    dom_ms, dom_launches = legendre[dom]
-    flops = S * (3.0 * dom_launches + 4.0 * B * a.steps)
-    achieved = flops / (dom_ms * 1e-3) / 1e12
-    kernel_key = "legendre_anal_kernel" if dom == "legendre_anal" else "legendre_synth_kernel"
-    traffic = traffic_from_profiles(kernel_key)
-    roofline = {"bound": "alu", "pipe": "fp64", "kernel": kernel_key, "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe %.3f TF/s"
-                               % (nsm, SM_MAX_MHZ, probe_tf),
-                "work": "7 flops per (l, m, ring-pair) step over the full triangle, per map (3 recurrence "
-                        "+ 4 accumulate); the kernel skips steps whose lambda is below 2^-224, so frac "
-                        "can exceed 1"}
-    launches = sum(v[1] for v in stages.values())
-
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
@@ -312,9 +369,14 @@ def ours_arm(a, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": DATA,
+            "vs_baseline": None,
+            "dtype": "f64 recurrence; bf16 digits (tcgen05, f32 accum) + f32 double-float sums" if a.mode == "split"
+                     else "f64",
+            "data": DATA,
             "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": L, "mmax": L,
-                       "maps_per_step": B, "mode": "plain FP64", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "maps_per_step": B, "mode": MODES[a.mode],
+                       "accuracy": "<= 1e-9 of the RMS vs the oracle" if a.mode == "split" else "<= 1e-11 of the RMS",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (a_lm %.2f GB, maps %.2f GB per step)"
                              % (B * nalm * 16 / 1e9, B * npix * 8 / 1e9),
                        "plan_create_s": plan_s},
@@ -322,6 +384,7 @@ def ours_arm(a, rank, world, local_rank):
                            "per": "step (%d-map round trip)" % B},
             "roofline": roofline,
             "stages_ms_per_step": {k: v[0] / a.steps for k, v in stages.items()},
+            "plain": plain,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
