@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--mode", default="split", choices=["split", "fp64"],
                     help="split: tensor-core synthesis + double-float analysis (<= 1e-9); fp64: plain")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
     return ap.parse_args()
 
 
@@ -131,9 +133,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle on bounded samples
 
-def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0):
+def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0, alm=None, smap=None):
     """Time the oracle on `nrings_sample` rings of alm2map and `nm_sample` values of m of
-    map2alm; return (estimated seconds per map round trip, description, threads)."""
+    map2alm; return (estimated seconds per map round trip, description, sample) where sample
+    holds the rings, the values of m and the oracle's outputs there (for accuracy checks)."""
     import numpy as np
 
     import oracle
@@ -142,20 +145,20 @@ def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0):
 
     geom = geometry.healpix(nside)
     R = len(geom[0])
-    a = inputs.gaussian_alm(lmax, lmax, seed=100)[0]
+    a = inputs.gaussian_alm(lmax, lmax, seed=100)[0] if alm is None else alm
     rings = [int((offset + (k + 0.5) * R / nrings_sample)) % R for k in range(nrings_sample)]
     t0 = time.perf_counter()
-    oracle.alm2map_rings(geom, a, lmax, lmax, rings)
+    ring_vals = oracle.alm2map_rings(geom, a, lmax, lmax, rings)
     t1 = time.perf_counter()
-    s = inputs.white_map(int(np.sum(geom[0])), seed=101)[0]
+    s = inputs.white_map(int(np.sum(geom[0])), seed=101)[0] if smap is None else smap
     ms = [int((offset * 7 + (k + 0.5) * (lmax + 1) / nm_sample)) % (lmax + 1) for k in range(nm_sample)]
     t2 = time.perf_counter()
-    oracle.map2alm_ms(geom, s, lmax, ms)
+    alm_vals = oracle.map2alm_ms(geom, s, lmax, ms)
     t3 = time.perf_counter()
     est = (t1 - t0) * R / nrings_sample + (t3 - t2) * (lmax + 1) / nm_sample
     desc = ("oracle alm2map on %d of %d rings (%.1f s) + map2alm on %d of %d values of m (%.1f s), "
             "scaled to one full round trip" % (nrings_sample, R, t1 - t0, nm_sample, lmax + 1, t3 - t2))
-    return est, desc
+    return est, desc, {"rings": rings, "ring_vals": ring_vals, "ms": ms, "alm_vals": alm_vals}
 
 
 def host_threads():
@@ -174,7 +177,7 @@ def reference_arm(a, rank, world):
     per_step = []
     desc = ""
     for i in range(a.warmup + a.steps):
-        est, desc = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, offset=i)
+        est, desc, _ = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, offset=i)
         if i >= a.warmup:
             per_step.append(est)
     mean_s = statistics.mean(per_step)
@@ -356,13 +359,56 @@ def ours_arm(a, rank, world, local_rank):
         e2e = {"value": job_throughput(world, B * a.steps, ems), "unit": "maps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    # accuracy of the precision form: against the plain FP64 path on the whole timed batch, both
+    # directions on the same inputs (max |x - x_plain| / RMS(x_plain), worst map)
+    accuracy = None
+    if a.mode == "split":
+        def rel_maps(x, ref):
+            d = (x - ref).abs().amax(dim=1)
+            r = ref.abs().pow(2).mean(dim=1).sqrt()
+            return float((d / r).max())
+
+        plan.set_mode(sht.MODE_FP64)
+        plan.alm2map(alm, out=mp)
+        plan.map2alm(mp, out=alm_out)
+        alm_plain = alm_out.clone()
+        plan.set_mode(sht.MODE_SPLIT_BF16)
+        map_split = torch.empty_like(mp)
+        plan.alm2map(alm, out=map_split)
+        plan.map2alm(mp, out=alm_out)          # analysis of the plain map: the same input both ways
+        torch.cuda.synchronize()
+        accuracy = {"split_vs_plain_fp64": {"alm2map": rel_maps(map_split, mp), "map2alm": rel_maps(alm_out, alm_plain),
+                                            "maps": B, "measure": "max|x - x_plain| / RMS(x_plain), worst map"},
+                    "bar": 1e-9}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle
         oracle.build()
         nthr = host_threads()
-        est, desc = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1)
+        a0 = host_alm[0].numpy()
+        s0 = mp[0].cpu().numpy() if accuracy else None
+        est, desc, smp = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, alm=a0, smap=s0)
         cpu = {"value": 1.0 / est, "unit": "maps/s", "cores": nthr, "kind": "oracle", "sample": desc}
+        if accuracy:
+            # the same oracle outputs checked against map 0 of the batch (rings and m of the sample)
+            ofs = np.concatenate([[0], np.cumsum(np.asarray(geom[0], dtype=np.int64))])
+            pix = np.concatenate([np.arange(ofs[r], ofs[r + 1]) for r in smp["rings"]])
+            ref = smp["ring_vals"]
+            rms = np.sqrt(np.mean(ref ** 2))
+            got_s = map_split[0].cpu().numpy()[pix]
+            got_p = mp[0].cpu().numpy()[pix]
+            idx = np.concatenate([[sht.alm_index(L, l, m) for l in range(m, L + 1)] for m in smp["ms"]])
+            aref = np.concatenate(smp["alm_vals"])
+            arms = np.sqrt(np.mean(np.abs(aref) ** 2))
+            accuracy["vs_oracle_sampled"] = {
+                "alm2map_split": float(np.max(np.abs(got_s - ref)) / rms),
+                "alm2map_plain": float(np.max(np.abs(got_p - ref)) / rms),
+                "map2alm_split": float(np.max(np.abs(alm_out[0].cpu().numpy()[idx] - aref)) / arms),
+                "map2alm_plain": float(np.max(np.abs(alm_plain[0].cpu().numpy()[idx] - aref)) / arms),
+                "sample": "map 0: %d rings %s of alm2map; m = %s of map2alm (input: the plain map); "
+                          "normalised by the RMS of the oracle's sampled values" % (len(smp["rings"]), smp["rings"],
+                                                                                   smp["ms"])}
 
     if rank == 0:
         q = sorted(step_ms)
@@ -385,14 +431,95 @@ def ours_arm(a, rank, world, local_rank):
             "roofline": roofline,
             "stages_ms_per_step": {k: v[0] / a.steps for k, v in stages.items()},
             "plain": plain,
+            "accuracy": accuracy,
+            "serve": None,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
         }
+    del alm, mp, alm_out, host_alm
+    if accuracy:
+        del alm_plain, map_split
+    plan.close()
+    torch.cuda.empty_cache()
+    serve_res = serve_leg(a, rep, local_rank) if a.serve_requests > 0 else None
+    if rank == 0:
+        line["serve"] = serve_res
         print(json.dumps(line), flush=True)
     rep.close()
     return 0
+
+
+def serve_leg(a, rep, local_rank):
+    """A Poisson trace of alm2map / map2alm requests (lmax log-uniform over {256, ..., 4096} on
+    HEALPix nside = lmax/2, 1-32 maps each, C_l-shaped Gaussian a_lm or unit white-noise maps,
+    inputs resident on the device before their arrival), served twice: by the continuous-batching
+    server in the precision form on two streams, and by the plain FP64 path one request per call
+    in arrival order.  Latency = completion - arrival; maps/s = maps / (last completion - first
+    arrival)."""
+    import numpy as np
+    import torch
+
+    from paper_1106_0159_gb300 import inputs, serve, sht
+
+    g = np.random.Generator(np.random.PCG64(rep.seed(4242)))
+    lmaxes = [256, 512, 1024, 2048, 4096]
+    spec = []
+    for _ in range(a.serve_requests):
+        L = lmaxes[int(g.integers(len(lmaxes)))]
+        spec.append((serve.ALM2MAP if g.random() < 0.5 else serve.MAP2ALM, L, L // 2, int(g.integers(1, 33))))
+    offsets = [t for t, _ in serve.poisson_trace(a.serve_rate, len(spec), lambda i: i, seed=rep.seed(4244))]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(rep.seed(4243))
+    sds, datas = {}, []
+    for d, L, ns, n in spec:
+        if d == serve.ALM2MAP:
+            if L not in sds:
+                l, m = inputs.lm_arrays(L, L)
+                cl = 1.0 / (l * (l + 1.0) + 1.0)
+                sds[L] = (torch.from_numpy(np.where(m == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda(),
+                          torch.from_numpy(m != 0).cuda())
+            sd, mnz = sds[L]
+            re = torch.randn((n, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd
+            im = torch.randn((n, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd * mnz
+            datas.append(torch.complex(re, im))
+        else:
+            datas.append(torch.randn((n, 12 * ns * ns), dtype=torch.float64, device="cuda", generator=gen))
+    torch.cuda.synchronize()
+    keys = sorted(set((ns, L) for _, L, ns, _ in spec))
+
+    def run(mode, nstreams, batching):
+        be = serve.TorchBackend(mode=mode, nstreams=nstreams, budget_fraction=0.8)
+        warm_s = be.warm(keys, max_maps=32)
+        srv = serve.Server(be, max_batch_maps=32, nstreams=nstreams, batching=batching)
+        trace = [(t, serve.Request(d, L, ns, x, n)) for t, (d, L, ns, n), x in zip(offsets, spec, datas)]
+        rep.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        srv.run_trace(trace, timeout=600)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        st = srv.stats()
+        status = max(be.plan(k, s).device_status() for k in keys for s in range(nstreams))
+        be.close()
+        st.update({"plan_warm_s": warm_s, "device_status": status, "clocks": clk,
+                   "streams": nstreams, "batching": batching})
+        return st
+
+    served = run(sht.MODE_SPLIT_BF16, 2, True)
+    plain = run(sht.MODE_FP64, 1, False)
+    del datas
+    torch.cuda.empty_cache()
+    nmaps = sum(n for *_, n in spec)
+    return {"trace": "%d requests, Poisson %.2f/s, lmax log-uniform over %s (HEALPix nside = lmax/2), 1-32 maps "
+                     "each (%d maps), half alm2map half map2alm on average; inputs resident on the device"
+                     % (len(spec), a.serve_rate, lmaxes, nmaps),
+            "served": served, "plain": plain,
+            "served_over_plain_maps_per_s": served["maps_per_s"] / plain["maps_per_s"],
+            "served_form": "continuous batching, up to 32 maps of one plan and direction per call, 2 streams, "
+                           "precision form",
+            "plain_form": "one request per call in arrival order, 1 stream, plain FP64"}
 
 
 def main():

@@ -133,6 +133,17 @@ int     sht_plan_npairs(sht_plan_t plan);            /* ring slots after north/s
 size_t  sht_workspace_bytes(sht_plan_t plan, int nmaps); /* scratch the transforms need for nmaps maps */
 
 /*
+ * Grow the plan's device scratch now to sht_workspace_bytes(plan, nmaps), so
+ * that later calls with at most nmaps maps allocate nothing (a server keeps
+ * its plans resident this way; the paper's memory estimate of Section 4.1
+ * has the same parts: maps, a_lm and the Delta_m slabs).  Freeing a smaller
+ * old scratch waits for the device.  SHT_EINVAL for a null plan or
+ * nmaps < 1; SHT_ENOMEM (plan unchanged, old scratch released) when the
+ * allocation fails.  Host call; no kernel runs.
+ */
+sht_status sht_plan_reserve(sht_plan_t plan, int nmaps);
+
+/*
  * Grid helpers (pure host).  HEALPix (Gorski et al. 2005, the grid of
  * Section 5): 4 nside - 1 rings north to south, caller arrays of that length,
  * equal weights 4 pi / (12 nside^2).  Gauss-Legendre: nrings rings at the

@@ -383,6 +383,12 @@ size_t sht_workspace_bytes(sht_plan_t plan, int nmaps)
     return d + std::max(std::max(r, a), t);
 }
 
+sht_status sht_plan_reserve(sht_plan_t plan, int nmaps)
+{
+    if (!plan || nmaps < 1) return SHT_EINVAL;
+    return ensure_workspace(plan->p, sht_workspace_bytes(plan, nmaps));
+}
+
 sht_status sht_plan_set_mode(sht_plan_t plan, int mode)
 {
     if (!plan || (mode != SHT_MODE_FP64 && mode != SHT_MODE_SPLIT_BF16)) return SHT_EINVAL;

@@ -34,7 +34,7 @@ EXPORTS = (
     "sht_workspace_bytes", "sht_geom_healpix", "sht_geom_gauss_legendre",
     "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
-    "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status",
+    "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
@@ -88,6 +88,7 @@ def load():
             "sht_plan_set_mode": (I, [P, I]),
             "sht_plan_mode": (I, [P]),
             "sht_plan_device_status": (I, [P, P, I]),
+            "sht_plan_reserve": (I, [P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -228,6 +229,10 @@ class Plan:
 
     def workspace_bytes(self, nmaps: int) -> int:
         return int(load().sht_workspace_bytes(self._h, int(nmaps)))
+
+    def reserve(self, nmaps: int):
+        """Grow the plan's device scratch now so calls with <= nmaps maps allocate nothing."""
+        _check(load().sht_plan_reserve(self._h, int(nmaps)), self._h, "sht_plan_reserve")
 
     # -- tensor checks ------------------------------------------------------
     def _dev(self, t, dtype, tail, name):
