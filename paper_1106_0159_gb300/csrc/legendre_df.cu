@@ -122,24 +122,38 @@ __device__ __forceinline__ float2 shfl_xor_df(float2 v, int m)
 }
 
 // Reduce-scatter of DF_G double-float values per lane over the warp: every lane ends with the
-// warp total of value (lane & (DF_G - 1)).
+// warp total of value (lane & (DF_G - 1)).  The caller stores value i at v[i ^ (lane & 7)], so
+// that in every halving round the value a lane keeps and the one it sends sit in fixed
+// registers (no per-lane selects): after the round with partner lane ^ h, v[i] (i < h) holds
+// both lanes' sums of value i ^ (lane & 7).
 __device__ __forceinline__ float2 warp_reduce_scatter_df(float2 v[DF_G])
 {
-    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int h = DF_G / 2; h >= 1; h >>= 1) {
-        const bool up = (lane & h) != 0;
 #pragma unroll
-        for (int i = 0; i < h; ++i) {
-            const float2 send = up ? v[i] : v[i + h];
-            const float2 keep = up ? v[i + h] : v[i];
-            v[i] = df_add(keep, shfl_xor_df(send, h));
-        }
+        for (int i = 0; i < h; ++i) v[i] = df_add(v[i], shfl_xor_df(v[i + h], h));
     }
     float2 r = v[0];
     r = df_add(r, shfl_xor_df(r, 8));
     r = df_add(r, shfl_xor_df(r, 16));
     return r;
+}
+
+// v[i] <- v[i ^ b] for b = lane & 7 (three conditional swaps)
+__device__ __forceinline__ void xor_permute(float2 v[DF_G], int b)
+{
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) {
+        const bool sw = (b & h) != 0;
+#pragma unroll
+        for (int i = 0; i < DF_G; ++i) {
+            if ((i & h) == 0) {
+                const float2 a = v[i], c = v[i + h];
+                v[i] = sw ? c : a;
+                v[i + h] = sw ? a : c;
+            }
+        }
+    }
 }
 
 struct DfArgs {
@@ -238,12 +252,16 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
                 }
                 continue;
             }
+            // value i of this lane is step i ^ b, whose l - m parity is (i & 1) ^ (b & 1)
+            const int b = lane & (DF_G - 1);
+            xor_permute(yv, b);
+            const int pe = b & 1;
 #pragma unroll 4
             for (int n = 0; n < N; ++n) {
-                const float2 xe = S.X[0][n][tid], xo = S.X[1][n][tid];
+                const float2 xa = S.X[pe][n][tid], xb = S.X[pe ^ 1][n][tid];
                 float2 p[DF_G];
 #pragma unroll
-                for (int jj = 0; jj < DF_G; ++jj) p[jj] = df_mul(yv[jj], (jj & 1) ? xo : xe);  // l - m parity = jj's
+                for (int i = 0; i < DF_G; ++i) p[i] = df_mul(yv[i], (i & 1) ? xb : xa);
                 const float2 r = warp_reduce_scatter_df(p);
                 if (lane < DF_G) S.red[warp][j0 + lane][n] = r;
             }

@@ -6,27 +6,31 @@
 // [128 slots x l] . [l x 2 maps (re, im)], split by the parity of l - m into
 // E (even) and O (odd) so that Delta_N = E + O, Delta_S = E - O.
 //
-// Exactness.  Both operands are cut into S = 6 balanced base-128 digits:
-// v = 2^(E-6) sum_s d_s 2^(-7 s), |d_s| <= 65, with one scale exponent E per
-// (m, slot block) for the recurrence values y = lambda / c and one per
-// (m, map column) for c_lm a_lm.  The y exponent is the measured maximum of
-// |y| over the block and all l (tc_ymax_kernel, once per plan, running the
-// same recurrence): an a priori bound such as |lambda_lm| <= sqrt((2l+1)/4pi)
-// can leave the leading digits empty by ten bits and push the significant
-// bits into the small digit classes.
+// Exactness.  Both operands are cut into S = 7 balanced base-128 digits:
+// v = 2^(E-6) sum_s d_s 2^(-7 s), |d_s| <= 64 (48 bits, rounded), with one
+// scale exponent E per (m, slot block) for the recurrence values y = lambda / c
+// and one per (m, map column) for c_lm a_lm.  The y exponent is the measured
+// maximum of |y| over the block and all l (tc_ymax_kernel, once per plan,
+// running the same recurrence): an a priori bound such as
+// |lambda_lm| <= sqrt((2l+1)/4pi) can leave the leading digits empty by ten
+// bits and push the significant bits into the small digit classes.  One scale
+// per column is coarse for a red spectrum: at high l, c a is ~2^-12 of the
+// column maximum and keeps ~12 bits fewer, which is why 7 digits are used (with
+// 6 digits and products i + j <= 5 the map error reached 9e-10 of its RMS at
+// lmax = 4096, spread evenly in relative terms over all m).
 // Each digit d_s 2^(-7 s) is exact in bf16.  Products of digit pairs (i, j)
-// with i + j <= 5 are accumulated by tcgen05.mma (kind::f16, bf16 inputs,
+// with i + j <= 6 are accumulated by tcgen05.mma (kind::f16, bf16 inputs,
 // FP32 accumulators in tensor memory) into five accumulators per parity:
-// classes i + j = 0, 1, 2 and 3 each alone (class 0: integers below 2^24 for
-// up to 4096 terms, exact; classes 1-3: multiples of 2^-7w well inside 24
-// bits, exact in practice) and classes 4..5 together.  The tensor core sums
+// classes i + j = 0, 1, 2 and 3 each alone (class 0: integers of at most 2^24
+// for up to 4096 terms, exact; classes 1-3: multiples of 2^-7w well inside 24
+// bits, exact in practice) and classes 4..6 together.  The tensor core sums
 // the 16 products of one MMA exactly when they share one scale, but it aligns
 // a smaller addend to the accumulator and truncates: a probe showed products
 // 2^-14 below the rest of their sum keeping only ~16 bits, and with classes 3-5
 // merged the truncation bias reached 2.3e-9 of the output RMS at lmax = 4096
 // (1.3e-10 with class 3 apart).  The epilogue adds the five in FP64 and
-// applies 2^(E_y + E_a - 12).  Dropped products (i + j >= 6) and the 41-bit
-// truncation stay below 2^-33 of the largest term.  Five accumulators of N
+// applies 2^(E_y + E_a - 12).  Dropped products (i + j >= 7) and the 48-bit
+// rounding stay near 2^-48 of the largest term.  Five accumulators of N
 // columns per parity need 10 N <= 320 of the 512 tensor-memory columns, so
 // one CTA runs per SM.
 //
@@ -35,7 +39,7 @@
 //      (see legendre.cu), splits each y into digits with integer operations
 //      and stores them as two k-groups of the bf16 A tiles [parity][digit];
 //      the a_lm digit tiles (prepared by tc_split_b_kernel) are copied in;
-//   2. one thread issues the 2 x 21 MMAs (M = 128, N = 16 or 32, K = 16) and
+//   2. one thread issues the 2 x 28 MMAs (M = 128, N = 16 or 32, K = 16) and
 //      commits them to an mbarrier, which the next chunk waits on before
 //      overwriting the tiles.
 // Polar CTAs (Reinsch form, see legendre.cu) are left to the FP64 kernel.
@@ -49,7 +53,11 @@ namespace sht {
 namespace {
 
 constexpr int TC_T = 128;           // slots per CTA = MMA M
-constexpr int TC_S = 6;             // digits per operand
+#ifndef TC_DIGITS
+#define TC_DIGITS 7
+#endif
+constexpr int TC_S = TC_DIGITS;     // digits per operand
+static_assert(TC_S >= 6 && TC_S <= 7, "the digit split needs 53 - (7 S - 1) >= 1 and class-0 sums below 2^24");
 constexpr int TC_CH = 32;           // l per chunk: 16 even + 16 odd
 constexpr int TC_ATILE = 128 * 16 * 2;  // bytes of one [128 x 16] bf16 tile
 constexpr int RESCALE_THR = 1023 + 256;
@@ -110,23 +118,25 @@ __device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
     k = kk;
 }
 
-// |v| * 2^(41 - E), truncated, as S balanced base-128 digits (most significant first),
-// each returned as the float d_s * 2^(-7 s).  Integer pipe only.
+// |v| * 2^(B - E), B = 7 S - 1 bits, rounded to the nearest integer, as S balanced base-128
+// digits (most significant first), each returned as the float d_s * 2^(-7 s), so that
+// v = 2^(E - 6) sum_s d_s 2^(-7 s) whatever S is.  Integer pipe only.
 __device__ __forceinline__ void split_digits(double v, int E, float out[TC_S])
 {
+    constexpr int B = 7 * TC_S - 1;
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((bits >> 52) & 0x7ff);
     const bool neg = (bits >> 63) != 0;
     unsigned long long F = 0;
     if (ex != 0) {
-        const int sh = 1034 + E - ex;
+        const int sh = 1075 - B + E - ex;  // v = mant 2^(ex - 1075)
         const unsigned long long mant = (bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
         if (sh >= 64)
             F = 0;
-        else if (sh >= 12)
-            F = mant >> sh;
+        else if (sh >= 53 - B)
+            F = (mant + (1ull << (sh - 1))) >> sh;  // |v| < 2^E gives sh >= 53 - B, so F <= 2^B
         else
-            F = (1ull << 41) - 1;  // outside the bound: saturate
+            F = (1ull << B) - 1;  // outside the bound: saturate
     }
     int d[TC_S];
 #pragma unroll
@@ -216,6 +226,7 @@ struct TcArgs {
     const double *u, *s;
     const double *alpha, *cfac;
     const int *Ey;           // [mmax+1][nblk] scale exponent of y per slot block
+    const int *first;        // [mmax+1][nblk] first chunk with a kept y value (nch: none)
     int *Ea;                 // [mmax+1][N] scale exponent of c a
     const int64_t *chunk_base;  // [mmax+1] first chunk of each m
     const int *chunk_m;      // [total chunks] m of each chunk
@@ -295,12 +306,13 @@ __global__ void tc_split_b_kernel(TcArgs A)
 // ---------------------------------------------------------------- y scale per (m, slot block)
 
 // max over the block's slots and all l (terms kept: k = 0) of the biased exponent of y,
-// written as E with |y| < 2^E (-1000 when every value is dropped).  Same recurrence,
-// operation for operation, as tc_synth_kernel.
-__global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out)
+// written as E with |y| < 2^E (-1000 when every value is dropped), and the first chunk of 32 l
+// in which any slot keeps a value (every earlier chunk contributes exactly zero).  Same
+// recurrence, operation for operation, as tc_synth_kernel.
+__global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out, int *first_out)
 {
     __shared__ double s_al[TC_CH];
-    __shared__ int s_max;
+    __shared__ int s_max, s_first;
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
     const int tid = threadIdx.x;
@@ -308,7 +320,11 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out)
     const bool active = slot < A.nslots;
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
-    if (tid == 0) s_max = 0;
+    const int nch = (L - m + TC_CH) / TC_CH;
+    if (tid == 0) {
+        s_max = 0;
+        s_first = nch;
+    }
     double u = 0.0, y1 = 0.0, y2 = 0.0;
     int k = 0;
     if (active) {
@@ -317,8 +333,7 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out)
         sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
         y2 = -y0;
     }
-    int mx = 0;
-    const int nch = (L - m + TC_CH) / TC_CH;
+    int mx = 0, fc = nch;
     for (int c = 0; c < nch; ++c) {
         const int l0 = m + TC_CH * c;
         __syncthreads();
@@ -332,7 +347,10 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out)
                 const double y = fma(s_al[j], t, -y2);
                 y2 = y1;
                 y1 = y;
-                if (l0 + j <= L && !(scaled && k < 0)) mx = max(mx, dexp(y));
+                if (l0 + j <= L && !(scaled && k < 0)) {
+                    mx = max(mx, dexp(y));
+                    fc = min(fc, c);
+                }
             }
             if (scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
                 y1 *= 0x1p-512;
@@ -342,8 +360,12 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out)
         }
     }
     atomicMax(&s_max, active ? mx : 0);
+    atomicMin(&s_first, active ? fc : nch);
     __syncthreads();
-    if (tid == 0) Ey_out[m * A.nblk + blk] = s_max ? s_max - 1022 : -1000;
+    if (tid == 0) {
+        Ey_out[m * A.nblk + blk] = s_max ? s_max - 1022 : -1000;
+        first_out[m * A.nblk + blk] = s_first;
+    }
 }
 
 // ---------------------------------------------------------------- the synthesis kernel
@@ -394,6 +416,7 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
     const uint32_t tmem = *tslot;
 
     const int nch = (L - m + TC_CH) / TC_CH;
+    const int cfirst = A.first[m * A.nblk + blk];  // chunks before it hold only dropped values
     const int64_t chunk0 = A.chunk_base[m];
     const uint32_t idesc = umma_idesc<N>();
     bool ok = true;
@@ -402,12 +425,35 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
     for (int c = 0; c < nch; ++c) {
         const int l0 = m + TC_CH * c;
         if (tid < TC_CH) s_al[tid] = (l0 + tid <= L) ? A.alpha[base + (l0 - m) + tid] : 0.0;
-        // this chunk's a_lm digit tiles, prefetched into registers
-        constexpr int BV = TcTile<N>::B_CHUNK / 16 / TC_T;  // uint4 per thread
-        uint4 breg[BV];
-        const uint4 *bsrc = A.bdig + (chunk0 + c) * (TcTile<N>::B_CHUNK / 16);
+        if (c < cfirst) {  // recurrence only: every value of this chunk is dropped
+            __syncthreads();
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const bool scaled = __any_sync(0xffffffffu, k < 0);
 #pragma unroll
-        for (int i = 0; i < BV; ++i) breg[i] = bsrc[i * TC_T + tid];
+                for (int j = 16 * h; j < 16 * h + 16; ++j) {
+                    const double t = fma(-u, y1, y1);
+                    const double y = fma(s_al[j], t, -y2);
+                    y2 = y1;
+                    y1 = y;
+                }
+                if (scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                    y1 *= 0x1p-512;
+                    y2 *= 0x1p-512;
+                    k += 1;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // this chunk's a_lm digit tiles, prefetched into registers
+        constexpr int BTOT = TcTile<N>::B_CHUNK / 16;        // uint4 of the chunk's tiles
+        constexpr int BV = (BTOT + TC_T - 1) / TC_T;          // per thread, the last one partial
+        uint4 breg[BV];
+        const uint4 *bsrc = A.bdig + (chunk0 + c) * BTOT;
+#pragma unroll
+        for (int i = 0; i < BV; ++i)
+            if (i * TC_T + tid < BTOT) breg[i] = bsrc[i * TC_T + tid];
         __syncthreads();
 
 #pragma unroll 1
@@ -446,8 +492,8 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
                 y2 *= 0x1p-512;
                 k += 1;
             }
-            if (h == 0 && c > 0) {  // the previous chunk's MMAs still read the tiles
-                if (!mbar_wait(mbar, (uint32_t)((c - 1) & 1))) ok = false;
+            if (h == 0 && c > cfirst) {  // the previous chunk's MMAs still read the tiles
+                if (!mbar_wait(mbar, (uint32_t)((c - 1 - cfirst) & 1))) ok = false;
             }
             // k-group h of every A tile: core matrix (slot/8, h), row slot%8
             const int off = ((h * 16) + (tid >> 3)) * 128 + (tid & 7) * 16;
@@ -458,7 +504,8 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
             }
             if (h == 0) {
 #pragma unroll
-                for (int i = 0; i < BV; ++i) ((uint4 *)sB)[i * TC_T + tid] = breg[i];
+                for (int i = 0; i < BV; ++i)
+                    if (i * TC_T + tid < BTOT) ((uint4 *)sB)[i * TC_T + tid] = breg[i];
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");
@@ -476,7 +523,7 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
                     for (int i = 0; i <= w; ++i) {
                         const int j = w - i;
                         const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
-                        const bool first = (c == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
+                        const bool first = (c == cfirst) && (i == 0) && (w <= TcTile<N>::NACC - 1);
                         const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
                         const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
                         umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
@@ -489,8 +536,9 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
     }
 
     // wait (bounded) for the last committed MMAs, also on the error path, before TMEM is read or freed
-    if (committed >= 0 && !mbar_wait(mbar, (uint32_t)(committed & 1))) ok = false;
-    ok = __syncthreads_and(ok && committed == nch - 1);
+    if (committed >= 0 && !mbar_wait(mbar, (uint32_t)((committed - cfirst) & 1))) ok = false;
+    const bool any_mma = cfirst < nch;  // else every value was dropped and Delta is zero
+    ok = __syncthreads_and(ok && (any_mma ? committed == nch - 1 : committed < 0));
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
         // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block
@@ -500,7 +548,7 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
 #pragma unroll
             for (int n = 0; n < N; ++n) acc[eo][n] = 0.0;
 #pragma unroll
-        for (int eo = 0; eo < 2; ++eo) {
+        for (int eo = 0; eo < 2 && any_mma; ++eo) {
 #pragma unroll
             for (int cls = 0; cls < TcTile<N>::NACC; ++cls) {
 #pragma unroll
@@ -576,10 +624,11 @@ cudaError_t build_tc_scales(Plan &p)
     A.nblk = (p.nslots + TC_T - 1) / TC_T;
     A.lmax = p.lmax;
     A.mmax = p.mmax;
-    int *ey = nullptr;
-    cudaError_t e = cudaMalloc(&ey, sizeof(int) * (size_t)(p.mmax + 1) * A.nblk);
+    int *ey = nullptr;  // [2][mmax + 1][nblk]: y exponents, then first live chunks
+    const size_t n = (size_t)(p.mmax + 1) * A.nblk;
+    cudaError_t e = cudaMalloc(&ey, sizeof(int) * 2 * n);
     if (e != cudaSuccess) return e;
-    tc_ymax_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TC_T>>>(A, ey);
+    tc_ymax_kernel<<<(unsigned)n, TC_T>>>(A, ey, ey + n);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -611,6 +660,7 @@ cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 
     A.alpha = p.d_alpha;
     A.cfac = p.d_cfac;
     A.Ey = p.d_tc_Ey;
+    A.first = p.d_tc_Ey + (size_t)(p.mmax + 1) * ((p.nslots + TC_T - 1) / TC_T);
     A.chunk_base = p.d_tc_chunk_base;
     A.chunk_m = p.d_tc_chunk_m;
     A.status = p.d_status;

@@ -73,7 +73,7 @@ struct Plan {
     int64_t tc_total_chunks = 0;        // sum over m of ceil((lmax - m + 1) / 32)
     int64_t *d_tc_chunk_base = nullptr; // [mmax + 1]
     int *d_tc_chunk_m = nullptr;        // [tc_total_chunks]
-    int *d_tc_Ey = nullptr;             // [mmax + 1][slot blocks] scale exponent of y = lambda / c
+    int *d_tc_Ey = nullptr;             // [2][mmax + 1][slot blocks]: scale exponent of y = lambda / c, first live chunk
     int *d_status = nullptr;            // device status word (bounded waits that gave up)
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
