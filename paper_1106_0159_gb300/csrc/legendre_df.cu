@@ -12,8 +12,8 @@
 // about 2^-44 relative accuracy, far inside the 1e-9 bar of this form.
 //
 // CTA: one m, 256 ring slots (one per thread, 8 warps).  Sigma = D_N + D_S
-// and D = D_N - D_S for up to 16 maps (32 real columns) sit in shared memory
-// as double-float pairs.  Per group of 8 l, every lane forms its 8 products
+// and D = D_N - D_S for the maps of one launch (up to DF_GROUP, 2 real columns
+// each) sit in shared memory as double-float pairs.  Per group of 8 l, every lane forms its 8 products
 // per column and a warp reduce-scatter (TwoSum) leaves each lane the warp
 // total of one l; the eight warps' totals are added in shared memory and the
 // block's partial a_lm (times 1/c, as in the FP64 kernel) is written as a
@@ -33,6 +33,13 @@ namespace {
 constexpr int DF_T = 256;          // threads = slots per CTA
 constexpr int DF_CHL = 32;         // l per shared-memory chunk (multiple of 8)
 constexpr int DF_G = 8;            // l per reduce-scatter round
+// maps per launch (16, 8 or 4).  Fewer maps: less shared memory and more CTAs per SM, but the
+// FP64 recurrence runs once per launch.  lmax = 4096, HEALPix 2048, 16 maps on GB300: 16 maps per
+// launch 809 ms, 8 maps 677 ms (two CTAs of 8 warps per SM), 4 maps 781 ms.
+#ifndef DF_GROUP
+#define DF_GROUP 8
+#endif
+static_assert(DF_GROUP == 16 || DF_GROUP == 8 || DF_GROUP == 4, "DF_GROUP is 16, 8 or 4");
 constexpr int RESCALE_THR = 1023 + 256;
 constexpr double POLAR_SIN = 0.03;  // must match legendre.cu
 
@@ -170,7 +177,7 @@ struct DfArgs {
 template <int N>
 struct DfSmem {
     float2 X[2][N][DF_T];           // [parity: Sigma, D][column][slot]
-    float2 red[DF_T / 32][DF_CHL][N];
+    float2 red[DF_T / 32][N][DF_CHL];  // [warp][column][l]: l contiguous, no bank conflicts
     double al[DF_CHL];
 };
 
@@ -179,6 +186,7 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DfSmem<N> &S = *reinterpret_cast<DfSmem<N> *>(smem_raw);
+
     constexpr int NW = DF_T / 32;
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
             if (!__any_sync(0xffffffffu, live)) {
                 if (lane < DF_G) {
 #pragma unroll
-                    for (int n = 0; n < N; ++n) S.red[warp][j0 + lane][n] = make_float2(0.f, 0.f);
+                    for (int n = 0; n < N; ++n) S.red[warp][n][j0 + lane] = make_float2(0.f, 0.f);
                 }
                 continue;
             }
@@ -263,18 +271,18 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 #pragma unroll
                 for (int i = 0; i < DF_G; ++i) p[i] = df_mul(yv[i], (i & 1) ? xb : xa);
                 const float2 r = warp_reduce_scatter_df(p);
-                if (lane < DF_G) S.red[warp][j0 + lane][n] = r;
+                if (lane < DF_G) S.red[warp][n][j0 + lane] = r;
             }
         }
         __syncthreads();
         // add the warps, divide by c (the block reduction multiplies by it), write the block's partial
         for (int i = tid; i < nl * (N / 2); i += DF_T) {
             const int j = i % nl, g = i / nl;
-            float2 re = S.red[0][j][2 * g], im = S.red[0][j][2 * g + 1];
+            float2 re = S.red[0][2 * g][j], im = S.red[0][2 * g + 1][j];
 #pragma unroll
             for (int w = 1; w < NW; ++w) {
-                re = df_add(re, S.red[w][j][2 * g]);
-                im = df_add(im, S.red[w][j][2 * g + 1]);
+                re = df_add(re, S.red[w][2 * g][j]);
+                im = df_add(im, S.red[w][2 * g + 1][j]);
             }
             if (g < A.nmaps) {
                 A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.nalm + base + (l0 - m) + j] =
@@ -315,6 +323,8 @@ cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
 {
     const int smem = (int)sizeof(DfSmem<N>);
     cudaError_t e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)  // all of the unified L1 as shared memory: as many CTAs per SM as it holds
+        e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     legendre_anal_df_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), DF_T, smem, st>>>(A);
     return cudaGetLastError();
@@ -353,11 +363,13 @@ cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     int g0 = 0;
     while (g0 < nmaps) {
-        const int nm = std::min(16, nmaps - g0);
+        const int nm = std::min(DF_GROUP, nmaps - g0);
         A.nmaps = nm;
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial + (int64_t)g0 * p.nalm;
-        cudaError_t e = nm > 8 ? launch_df_group<32>(p, A, st) : launch_df_group<16>(p, A, st);
+        cudaError_t e = nm > 8 ? launch_df_group<32>(p, A, st)
+                        : nm > 4 ? launch_df_group<16>(p, A, st)
+                                 : launch_df_group<8>(p, A, st);
         ++*nlaunch;
         if (e != cudaSuccess) return e;
         g0 += nm;

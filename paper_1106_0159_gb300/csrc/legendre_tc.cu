@@ -34,14 +34,17 @@
 // columns per parity need 10 N <= 320 of the 512 tensor-memory columns, so
 // one CTA runs per SM.
 //
-// Per CTA (one m, 128 slots, one thread per slot), per chunk of 32 l:
-//   1. every thread runs 32 steps of the two-instruction y recurrence
-//      (see legendre.cu), splits each y into digits with integer operations
-//      and stores them as two k-groups of the bf16 A tiles [parity][digit];
-//      the a_lm digit tiles (prepared by tc_split_b_kernel) are copied in;
-//   2. one thread issues the 2 x 28 MMAs (M = 128, N = 16 or 32, K = 16) and
-//      commits them to an mbarrier, which the next chunk waits on before
-//      overwriting the tiles.
+// Per CTA (one m, 128 slots, 256 threads in two warp groups), per chunk of 32 l:
+//   1. the recurrence warps run 32 steps of the two-instruction y recurrence (see
+//      legendre.cu), one slot per thread, and write the values to a y stage in shared memory;
+//   2. the split warps cut each value into digits with integer and FP32 operations, store
+//      them as the bf16 A tiles [parity][digit] of the chunk's stage, copy in the a_lm digit
+//      tiles (prepared by tc_split_b_kernel), and one thread issues the 2 x 28 MMAs (M = 128,
+//      N = 16 or 32, K = 16) and commits them to the stage's mbarrier.
+// y values and tiles are double-buffered, so the FP64 recurrence of chunk c + 1 runs while
+// chunk c is split and multiplied: with one CTA per SM (tensor memory and shared memory
+// both allow one), a single warp group could not keep the FP64 pipe busy between its
+// integer work.
 // Polar CTAs (Reinsch form, see legendre.cu) are left to the FP64 kernel.
 #include "sht_internal.h"
 
@@ -118,45 +121,57 @@ __device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
     k = kk;
 }
 
-// |v| * 2^(B - E), B = 7 S - 1 bits, rounded to the nearest integer, as S balanced base-128
+// sum over the S digit positions of 64 * 128^s: added to a signed F in (-2^B, 2^B], it makes
+// every 7-bit field of the sum a digit plus 64 (the carries of the balanced representation are
+// those of the one addition)
+__host__ __device__ constexpr unsigned long long digit_bias()
+{
+    unsigned long long k = 0;
+    for (int i = 0; i < TC_S; ++i) k = k * 128 + 64;
+    return k;
+}
+
+// v * 2^(B - E), B = 7 S - 1 bits, rounded to the nearest integer, as S balanced base-128
 // digits (most significant first), each returned as the float d_s * 2^(-7 s), so that
-// v = 2^(E - 6) sum_s d_s 2^(-7 s) whatever S is.  Integer pipe only.
+// v = 2^(E - 6) sum_s d_s 2^(-7 s) whatever S is.  |d_s| <= 64, and each float has at most
+// 8 significant bits, so its upper 16 bits are its exact bf16.  Integer and FP32 pipes only:
+// a field u = d + 64 becomes a float by OR-ing it into 2^23 and one exact FMA.
 __device__ __forceinline__ void split_digits(double v, int E, float out[TC_S])
 {
     constexpr int B = 7 * TC_S - 1;
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((bits >> 52) & 0x7ff);
-    const bool neg = (bits >> 63) != 0;
-    unsigned long long F = 0;
+    long long Fs = 0;
     if (ex != 0) {
         const int sh = 1075 - B + E - ex;  // v = mant 2^(ex - 1075)
         const unsigned long long mant = (bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+        unsigned long long F;
         if (sh >= 64)
             F = 0;
         else if (sh >= 53 - B)
             F = (mant + (1ull << (sh - 1))) >> sh;  // |v| < 2^E gives sh >= 53 - B, so F <= 2^B
         else
             F = (1ull << B) - 1;  // outside the bound: saturate
+        Fs = (bits >> 63) ? -(long long)F : (long long)F;
     }
-    int d[TC_S];
+    const unsigned long long G = (unsigned long long)Fs + digit_bias();  // >= 0, top field <= 128
+    const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
 #pragma unroll
-    for (int s = TC_S - 1; s >= 1; --s) {
-        const int dd = (int)((F + 64ull) & 127ull) - 64;
-        F = (F - (unsigned long long)(long long)dd) >> 7;
-        d[s] = dd;
+    for (int i = 0; i < TC_S; ++i) {
+        const int j = TC_S - 1 - i;  // field index, least significant first
+        const int b0 = 7 * j;
+        uint32_t u;
+        if (j == TC_S - 1)
+            u = (b0 >= 32) ? (hi >> (b0 - 32)) : __funnelshift_r(lo, hi, b0);  // top field: no mask
+        else if (b0 + 7 <= 32)
+            u = (lo >> b0) & 127u;
+        else if (b0 >= 32)
+            u = (hi >> (b0 - 32)) & 127u;
+        else
+            u = __funnelshift_r(lo, hi, b0) & 127u;
+        const float sc = __int_as_float((127 - 7 * i) << 23);                   // 2^(-7 i)
+        out[i] = fmaf(__uint_as_float(0x4B000000u | u), sc, -8388672.0f * sc);  // (u - 64) 2^(-7 i)
     }
-    d[0] = (int)F;
-#pragma unroll
-    for (int s = 0; s < TC_S; ++s) {
-        const float f = (float)(neg ? -d[s] : d[s]);
-        out[s] = f * __int_as_float((127 - 7 * s) << 23);  // exact power of two
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
-{
-    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&p);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -216,7 +231,6 @@ struct TcTile {
     static constexpr int A_BYTES = 2 * TC_S * TC_ATILE;
     static constexpr int NACC = TC_NACC;                      // accumulators per parity
     static constexpr int TMEM_COLS = (2 * NACC * N <= 128) ? 128 : (2 * NACC * N <= 256) ? 256 : 512;
-    static constexpr int SMEM = A_BYTES + B_CHUNK + 1024;
 };
 
 struct TcArgs {
@@ -370,35 +384,86 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out, in
 
 // ---------------------------------------------------------------- the synthesis kernel
 
+// named barriers (id 0 is __syncthreads): count = threads taking part, a multiple of 32
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool bar_red_and(int id, int count, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+enum : int { BAR_REC = 1, BAR_FULL = 2, BAR_EMPTY = 4, BAR_SPLIT = 6 };  // FULL, EMPTY: one per stage
+
 template <int N>
-__global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
+struct TcWs {
+    static constexpr int A_BYTES = TcTile<N>::A_BYTES;                    // one stage of A tiles
+    static constexpr int B_CHUNK = TcTile<N>::B_CHUNK;                    // one stage of B tiles
+    static constexpr int Y_BYTES = TC_CH * TC_T * 8;                      // one stage of y values
+    static constexpr int OFF_B = 2 * A_BYTES;
+    static constexpr int OFF_Y = OFF_B + 2 * B_CHUNK;
+    static constexpr int OFF_BAR = OFF_Y + 2 * Y_BYTES;
+    static constexpr int SMEM = OFF_BAR + 64 + 1024;                      // + alignment slack
+};
+
+// Two warp groups per CTA (one m, 128 slots, 256 threads):
+//   recurrence warps 0-3: thread r runs the FP64 recurrence of slot r and writes each chunk's 32
+//     values (0 where dropped) to a double-buffered y stage in shared memory;
+//   split warps 4-7: thread r cuts slot r's values into digits, stores row r of the A tiles
+//     (double-buffered), copies the chunk's a_lm digit tiles, and thread 128 issues the MMAs and
+//     commits them to the stage's mbarrier; the same warps read tensor memory at the end.
+// Stages: the y buffer is handed over with named barriers (FULL: recurrence arrives, split
+// waits; EMPTY: split arrives, recurrence waits, only where a later chunk reuses the stage);
+// the A/B tiles of a stage are rewritten after the mbarrier of the MMAs that read them.
+template <int N>
+__global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;                                   // [2][S][128 x 16] bf16
-    unsigned char *sB = smem + TcTile<N>::A_BYTES;              // [2][S][N x 16] bf16
-    uint64_t *mbar = (uint64_t *)(sB + TcTile<N>::B_CHUNK);
-    uint32_t *tslot = (uint32_t *)(mbar + 1);
-    __shared__ double s_al[TC_CH];
+    using W = TcWs<N>;
+    unsigned char *sA = smem;                               // [stage][parity][digit][128 x 16] bf16
+    unsigned char *sB = smem + W::OFF_B;                    // [stage][parity][digit][N x 16] bf16
+    double *ybuf = (double *)(smem + W::OFF_Y);             // [stage][32 l][128 slots]
+    uint64_t *mbar = (uint64_t *)(smem + W::OFF_BAR);       // [stage]
+    uint32_t *tslot = (uint32_t *)(mbar + 2);
+    __shared__ double s_al[2][TC_CH];
 
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
     if (m <= A.mR && A.s[blk * TC_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int slot = blk * TC_T + tid;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bool rec = warp < 4;
+    const int r = rec ? tid : tid - TC_T;                   // slot within the block
+    const int slot = blk * TC_T + r;
     const bool active = slot < A.nslots;
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
-    const int Ey = A.Ey[m * A.nblk + blk];
+    const int nch = (L - m + TC_CH) / TC_CH;
+    const int cfirst = A.first[m * A.nblk + blk];           // chunks before it hold only dropped values
+    const int nlive = nch - cfirst;
 
-    double u = 0.0, y1 = 0.0, y2 = 0.0;
-    int k = 0;
-    if (active) {
-        u = A.u[slot];
-        double y0;
-        sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
-        y1 = 0.0;
-        y2 = -y0;
+    if (nlive <= 0) {  // every value dropped: Delta_m is zero on these rings
+        if (!rec && active) {
+            const int rn = A.slotN[slot], rs = A.slotS[slot];
+            const int64_t mstride = A.mmax + 1;
+            for (int g = 0; g < A.nmaps; ++g) {
+                double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+                if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
+                if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
+            }
+        }
+        return;
     }
 
     if (warp == 0) {
@@ -407,7 +472,8 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -415,180 +481,179 @@ __global__ void __launch_bounds__(TC_T) tc_synth_kernel(TcArgs A)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
 
-    const int nch = (L - m + TC_CH) / TC_CH;
-    const int cfirst = A.first[m * A.nblk + blk];  // chunks before it hold only dropped values
-    const int64_t chunk0 = A.chunk_base[m];
-    const uint32_t idesc = umma_idesc<N>();
     bool ok = true;
-    int committed = -1;  // last chunk whose MMAs were committed
-
-    for (int c = 0; c < nch; ++c) {
-        const int l0 = m + TC_CH * c;
-        if (tid < TC_CH) s_al[tid] = (l0 + tid <= L) ? A.alpha[base + (l0 - m) + tid] : 0.0;
-        if (c < cfirst) {  // recurrence only: every value of this chunk is dropped
-            __syncthreads();
+    if (rec) {
+        // ------------------------------------------------ recurrence group
+        double u = 0.0, y1 = 0.0, y2 = 0.0;
+        int k = 0;
+        if (active) {
+            u = A.u[slot];
+            double y0;
+            sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
+            y2 = -y0;
+        }
+        for (int c = 0; c < nch; ++c) {
+            const int l0 = m + TC_CH * c;
+            const int sa = c & 1;
+            if (r < TC_CH) s_al[sa][r] = (l0 + r <= L) ? A.alpha[base + (l0 - m) + r] : 0.0;
+            bar_sync(BAR_REC, TC_T);  // s_al[sa] written; s_al[sa] of chunk c - 2 read long ago
+            const int q = c - cfirst;  // live chunk index
+            double *yb = ybuf + (size_t)(q & 1) * TC_CH * TC_T;
+            if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), 2 * TC_T);  // the split group read chunk q - 2
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const bool scaled = __any_sync(0xffffffffu, k < 0);
+                const bool drop = scaled && k < 0;
 #pragma unroll
                 for (int j = 16 * h; j < 16 * h + 16; ++j) {
                     const double t = fma(-u, y1, y1);
-                    const double y = fma(s_al[j], t, -y2);
+                    const double y = fma(s_al[sa][j], t, -y2);
                     y2 = y1;
                     y1 = y;
+                    if (q >= 0) yb[j * TC_T + r] = drop ? 0.0 : y;
                 }
-                if (scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                if (drop && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
                     y1 *= 0x1p-512;
                     y2 *= 0x1p-512;
                     k += 1;
                 }
             }
-            __syncthreads();
-            continue;
+            if (q >= 0) bar_arrive(BAR_FULL + (q & 1), 2 * TC_T);
         }
-        // this chunk's a_lm digit tiles, prefetched into registers
-        constexpr int BTOT = TcTile<N>::B_CHUNK / 16;        // uint4 of the chunk's tiles
-        constexpr int BV = (BTOT + TC_T - 1) / TC_T;          // per thread, the last one partial
-        uint4 breg[BV];
-        const uint4 *bsrc = A.bdig + (chunk0 + c) * BTOT;
+    } else {
+        // ------------------------------------------------ split / MMA group
+        const uint32_t idesc = umma_idesc<N>();
+        const int64_t chunk0 = A.chunk_base[m];
+        const int Ey = A.Ey[m * A.nblk + blk];
+        constexpr int BTOT = TcTile<N>::B_CHUNK / 16;   // uint4 of one chunk's B tiles
+        constexpr int BV = (BTOT + TC_T - 1) / TC_T;
+        for (int q = 0; q < nlive; ++q) {
+            const int c = cfirst + q;
+            const int st = q & 1;
+            unsigned char *a_st = sA + st * W::A_BYTES;
+            unsigned char *b_st = sB + st * W::B_CHUNK;
+            uint4 breg[BV];
+            const uint4 *bsrc = A.bdig + (chunk0 + c) * BTOT;
 #pragma unroll
-        for (int i = 0; i < BV; ++i)
-            if (i * TC_T + tid < BTOT) breg[i] = bsrc[i * TC_T + tid];
-        __syncthreads();
-
+            for (int i = 0; i < BV; ++i)
+                if (i * TC_T + r < BTOT) breg[i] = bsrc[i * TC_T + r];
+            // the MMAs of chunk q - 2 read this stage's tiles: wait (bounded) before rewriting them
+            if (q >= 2 && ok && !mbar_wait(&mbar[st], (uint32_t)(((q >> 1) - 1) & 1))) ok = false;
+            bar_sync(BAR_FULL + st, 2 * TC_T);  // y of chunk q is in its stage
+            const double *yb = ybuf + (size_t)st * TC_CH * TC_T;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            uint32_t pe[TC_S][4], po[TC_S][4];  // 8 even / 8 odd values per digit, bf16 pairs
-            const bool scaled = __any_sync(0xffffffffu, k < 0);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t pe[TC_S][4], po[TC_S][4];  // 8 even / 8 odd values per digit, bf16 pairs
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float de[TC_S], dd[TC_S];
+                for (int qq = 0; qq < 8; ++qq) {
+                    float de[TC_S], dd[TC_S];
+                    split_digits(yb[(16 * h + 2 * qq) * TC_T + r], Ey, de);
+                    split_digits(yb[(16 * h + 2 * qq + 1) * TC_T + r], Ey, dd);
+                    // the digit floats are bf16-exact: a bf16 pair is the upper halves of two floats
+                    if ((qq & 1) == 0) {
 #pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    const int j = 16 * h + 2 * q + par;
-                    const double t = fma(-u, y1, y1);
-                    const double y = fma(s_al[j], t, -y2);
-                    y2 = y1;
-                    y1 = y;
-                    const double yv = (scaled && k < 0) ? 0.0 : y;
-                    split_digits(yv, Ey, par ? dd : de);
-                }
-                if ((q & 1) == 0) {
+                        for (int s = 0; s < TC_S; ++s) {
+                            pe[s][qq >> 1] = __float_as_uint(de[s]);
+                            po[s][qq >> 1] = __float_as_uint(dd[s]);
+                        }
+                    } else {
 #pragma unroll
-                    for (int s = 0; s < TC_S; ++s) {
-                        pe[s][q >> 1] = pack_bf16x2(de[s], 0.f);
-                        po[s][q >> 1] = pack_bf16x2(dd[s], 0.f);
-                    }
-                } else {
-#pragma unroll
-                    for (int s = 0; s < TC_S; ++s) {
-                        pe[s][q >> 1] = (pe[s][q >> 1] & 0xFFFFu) | (pack_bf16x2(de[s], 0.f) << 16);
-                        po[s][q >> 1] = (po[s][q >> 1] & 0xFFFFu) | (pack_bf16x2(dd[s], 0.f) << 16);
+                        for (int s = 0; s < TC_S; ++s) {
+                            pe[s][qq >> 1] = __byte_perm(pe[s][qq >> 1], __float_as_uint(de[s]), 0x7632);
+                            po[s][qq >> 1] = __byte_perm(po[s][qq >> 1], __float_as_uint(dd[s]), 0x7632);
+                        }
                     }
                 }
-            }
-            if (scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
-                y1 *= 0x1p-512;
-                y2 *= 0x1p-512;
-                k += 1;
-            }
-            if (h == 0 && c > cfirst) {  // the previous chunk's MMAs still read the tiles
-                if (!mbar_wait(mbar, (uint32_t)((c - 1 - cfirst) & 1))) ok = false;
-            }
-            // k-group h of every A tile: core matrix (slot/8, h), row slot%8
-            const int off = ((h * 16) + (tid >> 3)) * 128 + (tid & 7) * 16;
+                if (h == 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, 2 * TC_T);  // y stage read
+                // k-group h of every A tile: core matrix (slot/8, h), row slot%8
+                const int off = ((h * 16) + (r >> 3)) * 128 + (r & 7) * 16;
 #pragma unroll
-            for (int s = 0; s < TC_S; ++s) {
-                *(uint4 *)(sA + (0 * TC_S + s) * TC_ATILE + off) = make_uint4(pe[s][0], pe[s][1], pe[s][2], pe[s][3]);
-                *(uint4 *)(sA + (1 * TC_S + s) * TC_ATILE + off) = make_uint4(po[s][0], po[s][1], po[s][2], po[s][3]);
+                for (int s = 0; s < TC_S; ++s) {
+                    *(uint4 *)(a_st + (0 * TC_S + s) * TC_ATILE + off) = make_uint4(pe[s][0], pe[s][1], pe[s][2], pe[s][3]);
+                    *(uint4 *)(a_st + (1 * TC_S + s) * TC_ATILE + off) = make_uint4(po[s][0], po[s][1], po[s][2], po[s][3]);
+                }
             }
-            if (h == 0) {
 #pragma unroll
-                for (int i = 0; i < BV; ++i)
-                    if (i * TC_T + tid < BTOT) ((uint4 *)sB)[i * TC_T + tid] = breg[i];
+            for (int i = 0; i < BV; ++i)
+                if (i * TC_T + r < BTOT) ((uint4 *)b_st)[i * TC_T + r] = breg[i];
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            ok = bar_red_and(BAR_SPLIT, TC_T, ok);
+            if (ok && r == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
+#pragma unroll
+                for (int eo = 0; eo < 2; ++eo) {
+#pragma unroll
+                    for (int w = 0; w <= TC_MAXW; ++w) {
+#pragma unroll
+                        for (int i = 0; i <= w; ++i) {
+                            const int j = w - i;
+                            const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
+                            const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
+                            const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
+                            const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
+                            umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
+                        }
+                    }
+                }
+                umma_commit(&mbar[st]);
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        // the last commit covers every MMA this thread issued: wait (bounded) before TMEM is read
+        if (ok && !mbar_wait(&mbar[(nlive - 1) & 1], (uint32_t)(((nlive - 1) >> 1) & 1))) ok = false;
+        ok = bar_red_and(BAR_SPLIT, TC_T, ok);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block
+            const int lw = warp & 3;  // this warp may read lanes 32 lw .. 32 lw + 31
+            double acc[2][N];
+#pragma unroll
+            for (int eo = 0; eo < 2; ++eo)
+#pragma unroll
+                for (int n = 0; n < N; ++n) acc[eo][n] = 0.0;
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo) {
 #pragma unroll
-                for (int w = 0; w <= TC_MAXW; ++w) {
+                for (int cls = 0; cls < TcTile<N>::NACC; ++cls) {
 #pragma unroll
-                    for (int i = 0; i <= w; ++i) {
-                        const int j = w - i;
-                        const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
-                        const bool first = (c == cfirst) && (i == 0) && (w <= TcTile<N>::NACC - 1);
-                        const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
-                        const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
-                        umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
+                    for (int n0 = 0; n0 < N; n0 += 16) {
+                        uint32_t v[16];
+                        const uint32_t addr =
+                            tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)((eo * TcTile<N>::NACC + cls) * N + n0);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                            "[%16];"
+                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                              "=r"(v[14]), "=r"(v[15])
+                            : "r"(addr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) acc[eo][n0 + t] += (double)__uint_as_float(v[t]);
                     }
                 }
             }
-            umma_commit(mbar);
-        }
-        committed = c;
-    }
-
-    // wait (bounded) for the last committed MMAs, also on the error path, before TMEM is read or freed
-    if (committed >= 0 && !mbar_wait(mbar, (uint32_t)((committed - cfirst) & 1))) ok = false;
-    const bool any_mma = cfirst < nch;  // else every value was dropped and Delta is zero
-    ok = __syncthreads_and(ok && (any_mma ? committed == nch - 1 : committed < 0));
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
-        // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block
-        double acc[2][N];
+            if (active) {
+                const int rn = A.slotN[slot], rs = A.slotS[slot];
+                const int64_t mstride = A.mmax + 1;
 #pragma unroll
-        for (int eo = 0; eo < 2; ++eo)
-#pragma unroll
-            for (int n = 0; n < N; ++n) acc[eo][n] = 0.0;
-#pragma unroll
-        for (int eo = 0; eo < 2 && any_mma; ++eo) {
-#pragma unroll
-            for (int cls = 0; cls < TcTile<N>::NACC; ++cls) {
-#pragma unroll
-                for (int n0 = 0; n0 < N; n0 += 16) {
-                    uint32_t r[16];
-                    const uint32_t addr =
-                        tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((eo * TcTile<N>::NACC + cls) * N + n0);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                        "[%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(addr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[eo][n0 + q] += (double)__uint_as_float(r[q]);
+                for (int g = 0; g < N / 2; ++g) {
+                    if (g < A.nmaps) {
+                        const double sr = pow2i_safe(Ey + A.Ea[m * N + 2 * g] - 12);
+                        const double si = pow2i_safe(Ey + A.Ea[m * N + 2 * g + 1] - 12);
+                        const double er = acc[0][2 * g] * sr, ei = acc[0][2 * g + 1] * si;
+                        const double orr = acc[1][2 * g] * sr, oi = acc[1][2 * g + 1] * si;
+                        double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+                        if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
+                        if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
+                    }
                 }
             }
+        } else if (r == 0) {
+            atomicOr(A.status, 1);
         }
-        if (active) {
-            const int rn = A.slotN[slot], rs = A.slotS[slot];
-            const int64_t mstride = A.mmax + 1;
-#pragma unroll
-            for (int g = 0; g < N / 2; ++g) {
-                if (g < A.nmaps) {
-                    const double sr = pow2i_safe(Ey + A.Ea[m * N + 2 * g] - 12);
-                    const double si = pow2i_safe(Ey + A.Ea[m * N + 2 * g + 1] - 12);
-                    const double er = acc[0][2 * g] * sr, ei = acc[0][2 * g + 1] * si;
-                    const double orr = acc[1][2 * g] * sr, oi = acc[1][2 * g + 1] * si;
-                    double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-                    if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
-                    if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
-                }
-            }
-        }
-    } else if (tid == 0) {
-        atomicOr(A.status, 1);
     }
-    (void)lane;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -601,12 +666,13 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
     const int64_t nchunks = p.tc_total_chunks;
     tc_scale_kernel<N><<<p.mmax + 1, 256, 0, st>>>(A);
     tc_split_b_kernel<N><<<(unsigned)nchunks, 256, 0, st>>>(A);
-    // at least 100 KB of shared memory per CTA keeps two CTAs per SM, which is what the
-    // tensor memory holds (TMEM_COLS <= 256 of 512 columns each)
-    const int smem = std::max(TcTile<N>::SMEM, TcTile<N>::TMEM_COLS > 256 ? 160 * 1024 : 100 * 1024);
+    // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
+    // and its accumulators take more than half of the tensor memory
+    static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");
+    const int smem = TcWs<N>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(tc_synth_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), TC_T, smem, st>>>(A);
+    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), 2 * TC_T, smem, st>>>(A);
     return cudaGetLastError();
 }
 
