@@ -1,17 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: alm2map + map2alm round trips at lmax = mmax = 4096 on HEALPix
-Nside = 2048 (50,331,648 pixels), a batch of maps per step, FP64.
+Nside = 2048 (50,331,648 pixels), a batch of maps per step.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode split|fp64]
 
 One step = sht_alm2map of B maps followed by sht_map2alm of the result
-(B = --maps, default 16).  `value` is maps per second (round trips) over the
-whole job with inputs resident in HBM; `e2e` is the same metric with the
-host->device copy of each step's a_lm (pinned) and the device->host read of
-its result inside the timed region.  For N > 1 (torchrun) every rank runs an
-independent replica of the workload; the barrier-bracketed time is the max
-over ranks.  `--impl reference` times the CPU oracle on this host's cores on
-bounded samples of the same workload.
+(B = --maps, default 16), in the precision form by default (FP64
+recurrence, tensor-core synthesis sum, double-float analysis sum).  `value`
+is maps per second (round trips) over the whole job with inputs resident in
+HBM; `e2e` is the same metric with the host->device copy of each step's a_lm
+(pinned) and the device->host read of its result inside the timed region.
+The same line carries the plain FP64 form measured in the same run (`plain`),
+the precision form's error against the plain path and the oracle
+(`accuracy`), a Poisson serving trace served by the continuous-batching
+server against the plain one-at-a-time path (`serve`: maps/s at saturation,
+p50/p99 latency at the offered rate) and the batched form (`batched`: 256
+maps of mixed lmax and direction as one CUDA graph, FP64 and precision form).
+For N > 1 (torchrun) every rank runs an independent replica of the workload;
+the barrier-bracketed time is the max over ranks.  `--impl reference` times
+the CPU oracle on this host's cores on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -60,6 +67,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
+    ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
     return ap.parse_args()
 
 
@@ -444,11 +452,104 @@ def ours_arm(a, rank, world, local_rank):
     plan.close()
     torch.cuda.empty_cache()
     serve_res = serve_leg(a, rep, local_rank) if a.serve_requests > 0 else None
+    batch_res = batch_leg(a, rep, local_rank) if a.batch_maps > 0 else None
     if rank == 0:
         line["serve"] = serve_res
+        line["batched"] = batch_res
         print(json.dumps(line), flush=True)
     rep.close()
     return 0
+
+
+def batch_leg(a, rep, local_rank):
+    """The batched form: `--batch-maps` maps, each with lmax drawn from {512, 1024, 2048} (HEALPix
+    nside = lmax/2) and alm2map or map2alm with probability 1/2, grouped into one call per
+    (lmax, direction) and run as one CUDA graph, plain FP64 and precision form side by side.
+    The knobs of every call are autotuned first (not timed); the graph replay and the same calls
+    made eagerly are timed with CUDA events, `--steps` times each after one warm-up."""
+    import functools
+
+    import numpy as np
+    import torch
+
+    from paper_1106_0159_gb300 import autotune, batch, inputs, sht
+
+    g = np.random.Generator(np.random.PCG64(rep.seed(5151)))
+    lmaxes = [512, 1024, 2048]
+    count = {}
+    for _ in range(a.batch_maps):
+        key = (lmaxes[int(g.integers(len(lmaxes)))], batch.ALM2MAP if g.random() < 0.5 else batch.MAP2ALM)
+        count[key] = count.get(key, 0) + 1
+    gen = torch.Generator(device="cuda")
+    out = {"maps": a.batch_maps, "calls": {"%s lmax=%d" % (d, L): n for (L, d), n in sorted(count.items())}}
+    for mode, name in ((sht.MODE_FP64, "fp64"), (sht.MODE_SPLIT_BF16, "precision")):
+        gen.manual_seed(rep.seed(5152))
+        plans = {}
+        for L in lmaxes:
+            plans[L] = sht.Plan(sht.healpix_geometry(L // 2), L, L, grid=sht.GRID_HEALPIX)
+            plans[L].set_mode(mode)
+        jobs = []
+        for (L, d), n in sorted(count.items()):
+            p = plans[L]
+            if d == batch.ALM2MAP:
+                lv, mv = inputs.lm_arrays(L, L)
+                cl = 1.0 / (lv * (lv + 1.0) + 1.0)
+                sd = torch.from_numpy(np.where(mv == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda()
+                mnz = torch.from_numpy(mv != 0).cuda()
+                x = torch.complex(torch.randn((n, p.nalm), dtype=torch.float64, device="cuda", generator=gen) * sd,
+                                  torch.randn((n, p.nalm), dtype=torch.float64, device="cuda", generator=gen) * sd * mnz)
+                y = torch.empty((n, p.npix), dtype=torch.float64, device="cuda")
+            else:
+                x = torch.randn((n, p.npix), dtype=torch.float64, device="cuda", generator=gen)
+                y = torch.empty((n, p.nalm), dtype=torch.complex128, device="cuda")
+            jobs.append(batch.Job(p, d, x, y))
+        tuner = autotune.Autotuner(timer=functools.partial(autotune.cuda_timer, reps=1))
+        t0 = time.perf_counter()
+        recs = [tuner.tune(j.plan, j.direction, j.src, j.dst) for j in jobs]
+        tune_s = time.perf_counter() - t0
+        b = batch.GraphBatch(jobs, nstreams=2)
+        t0 = time.perf_counter()
+        b.capture()
+        capture_s = time.perf_counter() - t0
+        stream = torch.cuda.current_stream()
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            rep.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return rep.max_over_ranks(e0.elapsed_time(e1), device="cuda") / a.steps
+
+        def eager():
+            b.run_eager(b.streams)
+            for st in b.streams:
+                stream.wait_stream(st)
+
+        def graph():
+            b.replay()
+
+        g_ms = timed(graph)
+        e_ms = timed(eager)
+        status = max(p.device_status() for p in plans.values())
+        out[name] = {"graph_ms": g_ms, "maps_per_s": a.batch_maps / (g_ms * 1e-3),
+                     "eager_ms": e_ms, "eager_maps_per_s": a.batch_maps / (e_ms * 1e-3),
+                     "tune_s": tune_s, "capture_s": capture_s, "device_status": status,
+                     "tuned": {"%s lmax=%d" % (j.direction, j.plan.lmax): {"knobs": r["knobs"], "ms": r["ms"],
+                                                                          "default_ms": r["default_ms"]}
+                               for j, r in zip(jobs, recs)}}
+        del b, jobs
+        for p in plans.values():
+            p.close()
+        torch.cuda.empty_cache()
+    out["precision_over_fp64"] = out["precision"]["maps_per_s"] / out["fp64"]["maps_per_s"]
+    out["form"] = ("one CUDA graph per batch: one library call per (lmax, direction), plans spread over 2 "
+                   "streams; knobs: maps or ring slots per launch, autotuned per call")
+    return out
 
 
 def serve_leg(a, rep, local_rank):
@@ -492,31 +593,35 @@ def serve_leg(a, rep, local_rank):
     def run(mode, nstreams, batching):
         be = serve.TorchBackend(mode=mode, nstreams=nstreams, budget_fraction=0.8)
         warm_s = be.warm(keys, max_maps=32)
-        srv = serve.Server(be, max_batch_maps=32, nstreams=nstreams, batching=batching)
-        trace = [(t, serve.Request(d, L, ns, x, n)) for t, (d, L, ns, n), x in zip(offsets, spec, datas)]
-        rep.barrier()
-        clocks = ClockSampler(local_rank)
-        clocks.start()
-        srv.run_trace(trace, timeout=600)
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-        st = srv.stats()
-        status = max(be.plan(k, s).device_status() for k in keys for s in range(nstreams))
+        out = {"plan_warm_s": warm_s, "streams": nstreams, "batching": batching}
+        for name, offs in (("open_loop", offsets), ("saturated", [0.0] * len(spec))):
+            srv = serve.Server(be, max_batch_maps=32, nstreams=nstreams, batching=batching)
+            trace = [(t, serve.Request(d, L, ns, x, n)) for t, (d, L, ns, n), x in zip(offs, spec, datas)]
+            rep.barrier()
+            clocks = ClockSampler(local_rank)
+            clocks.start()
+            srv.run_trace(trace, timeout=600)
+            torch.cuda.synchronize()
+            st = srv.stats()
+            st["clocks"] = clocks.stop()
+            out[name] = st
+        out["device_status"] = max(be.plan(k, s).device_status() for k in keys for s in range(nstreams))
         be.close()
-        st.update({"plan_warm_s": warm_s, "device_status": status, "clocks": clk,
-                   "streams": nstreams, "batching": batching})
-        return st
+        return out
 
     served = run(sht.MODE_SPLIT_BF16, 2, True)
     plain = run(sht.MODE_FP64, 1, False)
     del datas
     torch.cuda.empty_cache()
     nmaps = sum(n for *_, n in spec)
-    return {"trace": "%d requests, Poisson %.2f/s, lmax log-uniform over %s (HEALPix nside = lmax/2), 1-32 maps "
-                     "each (%d maps), half alm2map half map2alm on average; inputs resident on the device"
-                     % (len(spec), a.serve_rate, lmaxes, nmaps),
+    return {"trace": "%d requests, lmax log-uniform over %s (HEALPix nside = lmax/2), 1-32 maps each (%d maps), "
+                     "alm2map or map2alm with probability 1/2; inputs resident on the device. open_loop: Poisson "
+                     "arrivals at %.2f/s; saturated: all requests arrive at t = 0 (capacity)"
+                     % (len(spec), lmaxes, nmaps, a.serve_rate),
             "served": served, "plain": plain,
-            "served_over_plain_maps_per_s": served["maps_per_s"] / plain["maps_per_s"],
+            "maps_per_s": {"served": served["saturated"]["maps_per_s"], "plain": plain["saturated"]["maps_per_s"]},
+            "p99_ms": {"served": served["open_loop"]["p99_ms"], "plain": plain["open_loop"]["p99_ms"]},
+            "served_over_plain_maps_per_s": served["saturated"]["maps_per_s"] / plain["saturated"]["maps_per_s"],
             "served_form": "continuous batching, up to 32 maps of one plan and direction per call, 2 streams, "
                            "precision form",
             "plain_form": "one request per call in arrival order, 1 stream, plain FP64"}

@@ -144,6 +144,29 @@ size_t  sht_workspace_bytes(sht_plan_t plan, int nmaps); /* scratch the transfor
 sht_status sht_plan_reserve(sht_plan_t plan, int nmaps);
 
 /*
+ * Launch tuning.  The paper has none: its tile sizes are fixed by its kernel
+ * design.  Each knob bounds how many maps, or ring slots per thread, one
+ * kernel launch takes.  Synthesis results are identical for every setting,
+ * and the precision-form analysis is too (each map's sums keep their order).
+ * The FP64 analysis order of the ring sums changes with the slots per thread,
+ * so its results change within rounding.  The defaults are the settings
+ * measured best on GB300 at lmax = 4096.  The scratch a call needs follows the
+ * setting (sht_workspace_bytes); after a change, call sht_plan_reserve again
+ * if calls must not allocate.  Host calls; SHT_EINVAL for a null plan, an
+ * unknown knob or a value the knob does not take.
+ */
+typedef enum {
+    SHT_TUNE_SYNTH_MAPS = 0, /* FP64 synthesis: maps per launch, 1, 2 or 4 (default 4) */
+    SHT_TUNE_ANAL_MAPS = 1,  /* FP64 analysis: maps per launch, 1 or 2 (default 2) */
+    SHT_TUNE_ANAL_SLOTS = 2, /* FP64 analysis: ring slots per thread, 1 or 4 (default 4, or 1 below 512 slots) */
+    SHT_TUNE_DF_MAPS = 3,    /* precision-form analysis: maps per launch, 4, 8 or 16 (default 8) */
+    SHT_TUNE_TC_MAPS = 4,    /* precision-form synthesis: maps per tensor-core launch, 8 or 16 (default 16) */
+    SHT_TUNE_COUNT = 5
+} sht_tune;
+sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value);
+int sht_plan_tuning(sht_plan_t plan, int knob); /* the knob's value; -1 for a null plan or unknown knob */
+
+/*
  * Grid helpers (pure host).  HEALPix (Gorski et al. 2005, the grid of
  * Section 5): 4 nside - 1 rings north to south, caller arrays of that length,
  * equal weights 4 pi / (12 nside^2).  Gauss-Legendre: nrings rings at the

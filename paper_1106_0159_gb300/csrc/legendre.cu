@@ -504,7 +504,7 @@ __global__ void reduce_blocks_kernel(const double2 *__restrict__ partial, const 
     }
 }
 
-int anal_slots_per_cta(const Plan &p) { return p.nslots >= 4 * ANA_T ? 4 * ANA_T : ANA_T; }
+int anal_slots_per_cta(const Plan &p) { return p.tune[SHT_TUNE_ANAL_SLOTS] * ANA_T; }
 
 }  // namespace
 
@@ -534,10 +534,11 @@ cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *de
         const int left = nmaps - g0;
         A.alm = alm + (int64_t)g0 * p.nalm;
         A.delta = delta + (int64_t)g0 * dstride;
-        if (left >= 4) {
+        const int most = p.tune[SHT_TUNE_SYNTH_MAPS];
+        if (left >= 4 && most >= 4) {
             legendre_synth_kernel<4><<<grid, SYN_T, 0, st>>>(A);
             g0 += 4;
-        } else if (left >= 2) {
+        } else if (left >= 2 && most >= 2) {
             legendre_synth_kernel<2><<<grid, SYN_T, 0, st>>>(A);
             g0 += 2;
         } else {
@@ -580,10 +581,11 @@ cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, doubl
         const int left = nmaps - g0;
         A.alm = alm + (int64_t)g0 * p.nalm;
         A.delta = delta + (int64_t)g0 * dstride;
-        if (left >= 4) {
+        const int most = p.tune[SHT_TUNE_SYNTH_MAPS];
+        if (left >= 4 && most >= 4) {
             legendre_synth_kernel<4><<<grid, SYN_T, 0, st>>>(A);
             g0 += 4;
-        } else if (left >= 2) {
+        } else if (left >= 2 && most >= 2) {
             legendre_synth_kernel<2><<<grid, SYN_T, 0, st>>>(A);
             g0 += 2;
         } else {
@@ -648,6 +650,8 @@ size_t legendre_anal_partial_bytes(const Plan &p, int nmaps)
     return (size_t)nblk * (size_t)nmaps * (size_t)p.nalm * sizeof(double2);
 }
 
+int legendre_anal_default_slots(const Plan &p) { return p.nslots >= 4 * ANA_T ? 4 : 1; }
+
 int legendre_anal_nblk(const Plan &p)
 {
     const int per = anal_slots_per_cta(p);
@@ -683,7 +687,7 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *p
         const int left = nmaps - g0;
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = partial + (int64_t)g0 * p.nalm;
-        if (left >= 2) {
+        if (left >= 2 && p.tune[SHT_TUNE_ANAL_MAPS] >= 2) {
             if (per == 4 * ANA_T)
                 legendre_anal_kernel<2, 4><<<grid, ANA_T, 0, st>>>(A);
             else

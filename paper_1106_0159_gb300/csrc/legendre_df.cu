@@ -12,7 +12,7 @@
 // about 2^-44 relative accuracy, far inside the 1e-9 bar of this form.
 //
 // CTA: one m, 256 ring slots (one per thread, 8 warps).  Sigma = D_N + D_S
-// and D = D_N - D_S for the maps of one launch (up to DF_GROUP, 2 real columns
+// and D = D_N - D_S for the maps of one launch (up to SHT_TUNE_DF_MAPS, 2 real columns
 // each) sit in shared memory as double-float pairs.  Per group of 8 l, every lane forms its 8 products
 // per column and a warp reduce-scatter (TwoSum) leaves each lane the warp
 // total of one l; the eight warps' totals are added in shared memory and the
@@ -33,13 +33,9 @@ namespace {
 constexpr int DF_T = 256;          // threads = slots per CTA
 constexpr int DF_CHL = 32;         // l per shared-memory chunk (multiple of 8)
 constexpr int DF_G = 8;            // l per reduce-scatter round
-// maps per launch (16, 8 or 4).  Fewer maps: less shared memory and more CTAs per SM, but the
-// FP64 recurrence runs once per launch.  lmax = 4096, HEALPix 2048, 16 maps on GB300: 16 maps per
-// launch 809 ms, 8 maps 677 ms (two CTAs of 8 warps per SM), 4 maps 781 ms.
-#ifndef DF_GROUP
-#define DF_GROUP 8
-#endif
-static_assert(DF_GROUP == 16 || DF_GROUP == 8 || DF_GROUP == 4, "DF_GROUP is 16, 8 or 4");
+// Maps per launch: SHT_TUNE_DF_MAPS (16, 8 or 4; default 8).  Fewer maps: less shared memory and
+// more CTAs per SM, but the FP64 recurrence runs once per launch.  lmax = 4096, HEALPix 2048, 16 maps
+// on GB300: 16 maps per launch 809 ms, 8 maps 677 ms (two CTAs of 8 warps per SM), 4 maps 781 ms.
 constexpr int RESCALE_THR = 1023 + 256;
 constexpr double POLAR_SIN = 0.03;  // must match legendre.cu
 
@@ -319,18 +315,31 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
 }
 
 template <int N>
-cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
+cudaError_t configure_df()
 {
     const int smem = (int)sizeof(DfSmem<N>);
     cudaError_t e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)  // all of the unified L1 as shared memory: as many CTAs per SM as it holds
         e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    legendre_anal_df_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), DF_T, smem, st>>>(A);
+    return e;
+}
+
+template <int N>
+cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
+{
+    legendre_anal_df_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), DF_T, (int)sizeof(DfSmem<N>), st>>>(A);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t configure_df_kernels()
+{
+    cudaError_t e = configure_df<32>();
+    if (e == cudaSuccess) e = configure_df<16>();
+    if (e == cudaSuccess) e = configure_df<8>();
+    return e;
+}
 
 int legendre_anal_df_nblk(const Plan &p) { return (p.nslots + DF_T - 1) / DF_T; }
 
@@ -363,7 +372,7 @@ cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     int g0 = 0;
     while (g0 < nmaps) {
-        const int nm = std::min(DF_GROUP, nmaps - g0);
+        const int nm = std::min(p.tune[SHT_TUNE_DF_MAPS], nmaps - g0);
         A.nmaps = nm;
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial + (int64_t)g0 * p.nalm;

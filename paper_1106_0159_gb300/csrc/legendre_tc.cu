@@ -322,7 +322,8 @@ __global__ void tc_split_b_kernel(TcArgs A)
 // max over the block's slots and all l (terms kept: k = 0) of the biased exponent of y,
 // written as E with |y| < 2^E (-1000 when every value is dropped), and the first chunk of 32 l
 // in which any slot keeps a value (every earlier chunk contributes exactly zero).  Same
-// recurrence, operation for operation, as tc_synth_kernel.
+// recurrence, operation for operation (y' = (alpha x) y - y2 with alpha x = alpha - alpha u), as
+// tc_synth_kernel, so that both see the same rescaling steps.
 __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out, int *first_out)
 {
     __shared__ double s_al[TC_CH];
@@ -357,8 +358,8 @@ __global__ void __launch_bounds__(TC_T) tc_ymax_kernel(TcArgs A, int *Ey_out, in
         for (int h = 0; h < 2; ++h) {
             const bool scaled = __any_sync(0xffffffffu, k < 0);
             for (int j = 16 * h; j < 16 * h + 16; ++j) {
-                const double t = fma(-u, y1, y1);
-                const double y = fma(s_al[j], t, -y2);
+                const double ax = fma(-s_al[j], u, s_al[j]);  // alpha x, off the dependency chain
+                const double y = fma(ax, y1, -y2);
                 y2 = y1;
                 y1 = y;
                 if (l0 + j <= L && !(scaled && k < 0)) {
@@ -472,8 +473,9 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        // two issuing threads (one per parity) commit to each stage's mbarrier
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(2));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(2));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -506,8 +508,10 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
                 const bool drop = scaled && k < 0;
 #pragma unroll
                 for (int j = 16 * h; j < 16 * h + 16; ++j) {
-                    const double t = fma(-u, y1, y1);
-                    const double y = fma(s_al[sa][j], t, -y2);
+                    // alpha x = alpha (1 - u) does not depend on y, so each step adds one DFMA
+                    // (not two) to the dependency chain: one chain per SMSP is latency-bound
+                    const double ax = fma(-s_al[sa][j], u, s_al[sa][j]);
+                    const double y = fma(ax, y1, -y2);
                     y2 = y1;
                     y1 = y;
                     if (q >= 0) yb[j * TC_T + r] = drop ? 0.0 : y;
@@ -579,11 +583,11 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             ok = bar_red_and(BAR_SPLIT, TC_T, ok);
-            if (ok && r == 0) {
+            if (ok && (r & 31) == 0 && r < 64) {  // parity eo = r / 32: lane 0 of the first two split warps
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
-#pragma unroll
-                for (int eo = 0; eo < 2; ++eo) {
+                const int eo = r >> 5;
+                {
 #pragma unroll
                     for (int w = 0; w <= TC_MAXW; ++w) {
 #pragma unroll
@@ -669,14 +673,20 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
     // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
     // and its accumulators take more than half of the tensor memory
     static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");
-    const int smem = TcWs<N>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(tc_synth_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), 2 * TC_T, smem, st>>>(A);
+    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), 2 * TC_T, TcWs<N>::SMEM, st>>>(A);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t configure_tc_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(tc_synth_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcWs<32>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_synth_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcWs<16>::SMEM);
+    return e;
+}
 
 // Per-(m, slot block) y exponents for the precision form (synchronous, once per plan).
 cudaError_t build_tc_scales(Plan &p)
@@ -708,12 +718,12 @@ cudaError_t build_tc_scales(Plan &p)
 size_t tc_workspace_bytes(const Plan &p, int nmaps)
 {
     if (nmaps <= 0) return 0;
-    const int n = nmaps > 8 ? 32 : 16;
+    const int n = std::min(nmaps, p.tune[SHT_TUNE_TC_MAPS]) > 8 ? 32 : 16;
     const size_t bchunk = (size_t)2 * TC_S * n * 16 * 2;
     return (size_t)p.tc_total_chunks * bchunk + (size_t)(p.mmax + 1) * 32 * sizeof(int) + 256;
 }
 
-// Synthesis Legendre stage in the precision form; scratch holds tc_workspace_bytes(p, min(nmaps, 16)).
+// Synthesis Legendre stage in the precision form; scratch holds tc_workspace_bytes(p, nmaps).
 cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,
                                      cudaStream_t st, int *nlaunch)
 {
@@ -740,7 +750,7 @@ cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     int g0 = 0;
     while (g0 < nmaps) {
-        const int nm = std::min(16, nmaps - g0);
+        const int nm = std::min(p.tune[SHT_TUNE_TC_MAPS], nmaps - g0);
         A.nmaps = nm;
         A.alm = alm + (int64_t)g0 * p.nalm;
         A.delta = delta + (int64_t)g0 * dstride;

@@ -77,6 +77,9 @@ struct Plan {
     int *d_status = nullptr;            // device status word (bounded waits that gave up)
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
+    // launch tuning (sht_tune): maps or slots per thread per launch
+    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16};
+
     // workspace, grown on demand
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
@@ -103,6 +106,9 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *p
                                  int *nlaunch);
 cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *alm, int nmaps, cudaStream_t st);
 int legendre_anal_nblk(const Plan &p);
+int legendre_anal_default_slots(const Plan &p);  // default SHT_TUNE_ANAL_SLOTS for the plan's slot count
+cudaError_t configure_tc_kernels();              // one-time function attributes (not stream work)
+cudaError_t configure_df_kernels();
 size_t legendre_anal_partial_bytes(const Plan &p, int nmaps);
 cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                               cudaStream_t st);

@@ -279,7 +279,7 @@ sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, void 
 
 size_t synth_scratch_bytes(const Plan &p, int nmaps)
 {
-    return p.mode == SHT_MODE_SPLIT_BF16 ? sht::tc_workspace_bytes(p, std::min(nmaps, 16)) : 0;
+    return p.mode == SHT_MODE_SPLIT_BF16 ? sht::tc_workspace_bytes(p, nmaps) : 0;
 }
 
 size_t anal_partial_bytes(const Plan &p, int nmaps)
@@ -383,6 +383,29 @@ size_t sht_workspace_bytes(sht_plan_t plan, int nmaps)
     return d + std::max(std::max(r, a), t);
 }
 
+sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value)
+{
+    if (!plan) return SHT_EINVAL;
+    bool ok = false;
+    switch (knob) {
+    case SHT_TUNE_SYNTH_MAPS: ok = value == 1 || value == 2 || value == 4; break;
+    case SHT_TUNE_ANAL_MAPS: ok = value == 1 || value == 2; break;
+    case SHT_TUNE_ANAL_SLOTS: ok = value == 1 || value == 4; break;
+    case SHT_TUNE_DF_MAPS: ok = value == 4 || value == 8 || value == 16; break;
+    case SHT_TUNE_TC_MAPS: ok = value == 8 || value == 16; break;
+    default: ok = false;
+    }
+    if (!ok) return SHT_EINVAL;
+    plan->p.tune[knob] = value;
+    return SHT_OK;
+}
+
+int sht_plan_tuning(sht_plan_t plan, int knob)
+{
+    if (!plan || knob < 0 || knob >= SHT_TUNE_COUNT) return -1;
+    return plan->p.tune[knob];
+}
+
 sht_status sht_plan_reserve(sht_plan_t plan, int nmaps)
 {
     if (!plan || nmaps < 1) return SHT_EINVAL;
@@ -460,6 +483,7 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     std::vector<double3> rein;
     reinsch_tables(lmax, p.mR, rein);
     p.polar_first_slot = p.mR >= 0 && s[0] < 0.03;
+    p.tune[SHT_TUNE_ANAL_SLOTS] = sht::legendre_anal_default_slots(p);
     // precision form: 32-l chunks per m
     std::vector<int64_t> chunk_base(mmax + 1);
     int64_t nchunks = 0;
@@ -492,6 +516,11 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     if (e == cudaSuccess) e = upload(&p.d_ofs, p.ofs.data(), p.ofs.size());
     if (e == cudaSuccess) e = upload(&p.d_nphi, nphi32.data(), nphi32.size());
     if (e == cudaSuccess) e = upload(&p.d_w, p.w.data(), p.w.size());
+    if (e == cudaSuccess) {  // function attributes once, so that calls enqueue stream work only
+        where = "kernel attributes";
+        e = sht::configure_tc_kernels();
+        if (e == cudaSuccess) e = sht::configure_df_kernels();
+    }
     if (e == cudaSuccess) {
         where = "phase table";
         e = sht::build_phase_table(p);

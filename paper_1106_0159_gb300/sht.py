@@ -35,8 +35,13 @@ EXPORTS = (
     "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
+    "sht_plan_set_tuning", "sht_plan_tuning",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
+# launch tuning knobs (sht_tune) and the values each takes
+TUNE_SYNTH_MAPS, TUNE_ANAL_MAPS, TUNE_ANAL_SLOTS, TUNE_DF_MAPS, TUNE_TC_MAPS = 0, 1, 2, 3, 4
+TUNE_VALUES = {TUNE_SYNTH_MAPS: (1, 2, 4), TUNE_ANAL_MAPS: (1, 2), TUNE_ANAL_SLOTS: (1, 4),
+               TUNE_DF_MAPS: (4, 8, 16), TUNE_TC_MAPS: (8, 16)}
 STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
 
 
@@ -89,6 +94,8 @@ def load():
             "sht_plan_mode": (I, [P]),
             "sht_plan_device_status": (I, [P, P, I]),
             "sht_plan_reserve": (I, [P, I]),
+            "sht_plan_set_tuning": (I, [P, I, I]),
+            "sht_plan_tuning": (I, [P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -229,6 +236,13 @@ class Plan:
 
     def workspace_bytes(self, nmaps: int) -> int:
         return int(load().sht_workspace_bytes(self._h, int(nmaps)))
+
+    def set_tuning(self, knob: int, value: int):
+        """Set a launch-tuning knob (TUNE_*); see TUNE_VALUES for what each takes."""
+        _check(load().sht_plan_set_tuning(self._h, int(knob), int(value)), self._h, "sht_plan_set_tuning")
+
+    def tuning(self, knob: int) -> int:
+        return int(load().sht_plan_tuning(self._h, int(knob)))
 
     def reserve(self, nmaps: int):
         """Grow the plan's device scratch now so calls with <= nmaps maps allocate nothing."""
