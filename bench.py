@@ -341,31 +341,62 @@ def ours_arm(a, rank, world, local_rank):
                  "roofline": fp64_roofline(pr, a.plain_steps)}
         plan.set_mode(sht.MODE_SPLIT_BF16)
 
-    # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory
+    # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory, every
+    # step.  The copies run on a copy stream, double-buffered, so that step i + 1's upload and step
+    # i's download overlap step i's transforms (a pipeline over a stream of batches).  The timed
+    # region runs from the first upload to the last download.
     e2e = None
     if not a.no_e2e:
         host_out = torch.empty((B, nalm), dtype=torch.complex128).pin_memory()
+        copy = torch.cuda.Stream()
+        ins = [alm, torch.empty_like(alm)]
+        outs = [alm_out, torch.empty_like(alm_out)]
+        ev = torch.cuda.Event
 
-        def e2e_step():
-            alm.copy_(host_alm, non_blocking=True)
-            plan.alm2map(alm, out=mp)
-            plan.map2alm(mp, out=alm_out)
-            host_out.copy_(alm_out, non_blocking=True)
+        def run_pipeline(nsteps):
+            up = [ev(), ev()]          # upload of buffer b done
+            done = [ev(), ev()]        # transforms that read ins[b] / wrote outs[b] done
+            down = [ev(), ev()]        # download of outs[b] done
+            started = [False, False]
+            t0, t1 = ev(enable_timing=True), ev(enable_timing=True)
+            t0.record(copy)
+            with torch.cuda.stream(copy):
+                ins[0].copy_(host_alm, non_blocking=True)
+            up[0].record(copy)
+            for i in range(nsteps):
+                b = i & 1
+                if i + 1 < nsteps:  # next upload into the other buffer, once its last transforms finished
+                    nb = b ^ 1
+                    if started[nb]:
+                        copy.wait_event(done[nb])
+                    with torch.cuda.stream(copy):
+                        ins[nb].copy_(host_alm, non_blocking=True)
+                    up[nb].record(copy)
+                stream.wait_event(up[b])
+                if started[b]:
+                    stream.wait_event(down[b])  # outs[b] was read back
+                plan.alm2map(ins[b], out=mp)
+                plan.map2alm(mp, out=outs[b])
+                done[b].record(stream)
+                started[b] = True
+                copy.wait_event(done[b])
+                with torch.cuda.stream(copy):
+                    host_out.copy_(outs[b], non_blocking=True)
+                down[b].record(copy)
+            t1.record(copy)
+            return t0, t1
 
-        e2e_step()
+        run_pipeline(2)
         torch.cuda.synchronize()
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.steps):
-            e2e_step()
-        e1.record(stream)
+        t0, t1 = run_pipeline(a.steps)
         torch.cuda.synchronize()
         barrier()
-        ems = rep.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+        ems = rep.max_over_ranks(t0.elapsed_time(t1), device="cuda")
         nbytes = B * nalm * 16
         e2e = {"value": job_throughput(world, B * a.steps, ems), "unit": "maps/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "form": "uploads and downloads on a copy stream, double-buffered, overlapping the transforms"}
 
     # accuracy of the precision form: against the plain FP64 path on the whole timed batch, both
     # directions on the same inputs (max |x - x_plain| / RMS(x_plain), worst map)

@@ -473,9 +473,9 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        // two issuing threads (one per parity) commit to each stage's mbarrier
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(2));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(2));
+        // four issuing threads (parity x class group) commit to each stage's mbarrier
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(4));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(4));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -494,10 +494,17 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
             sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
             y2 = -y0;
         }
+        // alpha of the next chunk is loaded one chunk ahead (thread r < 32 holds entry r), so that
+        // its global-memory latency hides behind the current chunk's 32 steps
+        double al_next = (r < TC_CH && m + r <= L) ? A.alpha[base + r] : 0.0;
         for (int c = 0; c < nch; ++c) {
             const int l0 = m + TC_CH * c;
             const int sa = c & 1;
-            if (r < TC_CH) s_al[sa][r] = (l0 + r <= L) ? A.alpha[base + (l0 - m) + r] : 0.0;
+            if (r < TC_CH) {
+                s_al[sa][r] = al_next;
+                const int ln = l0 + TC_CH + r;
+                al_next = (c + 1 < nch && ln <= L) ? A.alpha[base + (ln - m)] : 0.0;
+            }
             bar_sync(BAR_REC, TC_T);  // s_al[sa] written; s_al[sa] of chunk c - 2 read long ago
             const int q = c - cfirst;  // live chunk index
             double *yb = ybuf + (size_t)(q & 1) * TC_CH * TC_T;
@@ -583,13 +590,18 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             ok = bar_red_and(BAR_SPLIT, TC_T, ok);
-            if (ok && (r & 31) == 0 && r < 64) {  // parity eo = r / 32: lane 0 of the first two split warps
+            // lane 0 of each split warp issues the MMAs of one (parity, class group): warp 4 + 2 eo
+            // the classes below NACC - 1 (10 MMAs), warp 5 + 2 eo the merged last class (18); each
+            // accumulator has one issuer, so its MMAs stay in order
+            if (ok && (r & 31) == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
-                const int eo = r >> 5;
+                const int eo = r >> 6;
+                const bool last_group = ((r >> 5) & 1) != 0;
                 {
 #pragma unroll
                     for (int w = 0; w <= TC_MAXW; ++w) {
+                        if ((w >= TcTile<N>::NACC - 1) != last_group) continue;
 #pragma unroll
                         for (int i = 0; i <= w; ++i) {
                             const int j = w - i;
