@@ -405,7 +405,7 @@ __device__ __forceinline__ bool bar_red_and(int id, int count, bool pred)
     return r != 0;
 }
 
-enum : int { BAR_REC = 1, BAR_FULL = 2, BAR_EMPTY = 4, BAR_SPLIT = 6 };  // FULL, EMPTY: one per stage
+enum : int { BAR_FULL = 2, BAR_EMPTY = 4, BAR_SPLIT = 6 };  // FULL, EMPTY: one per stage
 
 template <int N>
 struct TcWs {
@@ -418,17 +418,22 @@ struct TcWs {
     static constexpr int SMEM = OFF_BAR + 64 + 1024;                      // + alignment slack
 };
 
-// Two warp groups per CTA (one m, 128 slots, 256 threads):
+constexpr int TC_NT = 3 * TC_T;  // threads per synthesis CTA: 4 recurrence warps + 8 split warps
+
+// Warp groups per CTA (one m, 128 slots, 384 threads):
 //   recurrence warps 0-3: thread r runs the FP64 recurrence of slot r and writes each chunk's 32
-//     values (0 where dropped) to a double-buffered y stage in shared memory;
-//   split warps 4-7: thread r cuts slot r's values into digits, stores row r of the A tiles
-//     (double-buffered), copies the chunk's a_lm digit tiles, and thread 128 issues the MMAs and
-//     commits them to the stage's mbarrier; the same warps read tensor memory at the end.
+//     values (0 where dropped) to a double-buffered y stage in shared memory; alpha comes from a
+//     register of lane j (warp shuffle), loaded one chunk ahead;
+//   split warps 4-11: thread (par, r) cuts the 16 values of parity par of slot r into digits and
+//     stores row r of the parity's A tiles (double-buffered); all of them copy the chunk's a_lm
+//     digit tiles; lane 0 of warps 4-7 issues the MMAs of one (parity, class group) each and
+//     commits them to the stage's mbarrier; at the end they read tensor memory, warps 4-7 for
+//     the first half of the columns and warps 8-11 for the second.
 // Stages: the y buffer is handed over with named barriers (FULL: recurrence arrives, split
 // waits; EMPTY: split arrives, recurrence waits, only where a later chunk reuses the stage);
 // the A/B tiles of a stage are rewritten after the mbarrier of the MMAs that read them.
 template <int N>
-__global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
+__global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     using W = TcWs<N>;
@@ -437,15 +442,16 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
     double *ybuf = (double *)(smem + W::OFF_Y);             // [stage][32 l][128 slots]
     uint64_t *mbar = (uint64_t *)(smem + W::OFF_BAR);       // [stage]
     uint32_t *tslot = (uint32_t *)(mbar + 2);
-    __shared__ double s_al[2][TC_CH];
 
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
     if (m <= A.mR && A.s[blk * TC_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool rec = warp < 4;
-    const int r = rec ? tid : tid - TC_T;                   // slot within the block
+    const int sp = tid - TC_T;                              // split-thread index 0..255
+    const int r = rec ? tid : (sp & (TC_T - 1));            // slot within the block
+    const int par = rec ? 0 : (sp >> 7);                    // split threads: parity of l - m they cut
     const int slot = blk * TC_T + r;
     const bool active = slot < A.nslots;
     const int L = A.lmax;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
     const int nlive = nch - cfirst;
 
     if (nlive <= 0) {  // every value dropped: Delta_m is zero on these rings
-        if (!rec && active) {
+        if (!rec && par == 0 && active) {
             const int rn = A.slotN[slot], rs = A.slotS[slot];
             const int64_t mstride = A.mmax + 1;
             for (int g = 0; g < A.nmaps; ++g) {
@@ -494,21 +500,18 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
             sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
             y2 = -y0;
         }
-        // alpha of the next chunk is loaded one chunk ahead (thread r < 32 holds entry r), so that
-        // its global-memory latency hides behind the current chunk's 32 steps
-        double al_next = (r < TC_CH && m + r <= L) ? A.alpha[base + r] : 0.0;
+        // lane j holds alpha of step j of the current chunk and loads the next chunk's ahead
+        double al_next = (m + lane <= L) ? A.alpha[base + lane] : 0.0;
         for (int c = 0; c < nch; ++c) {
             const int l0 = m + TC_CH * c;
-            const int sa = c & 1;
-            if (r < TC_CH) {
-                s_al[sa][r] = al_next;
-                const int ln = l0 + TC_CH + r;
+            const double al_cur = al_next;
+            {
+                const int ln = l0 + TC_CH + lane;
                 al_next = (c + 1 < nch && ln <= L) ? A.alpha[base + (ln - m)] : 0.0;
             }
-            bar_sync(BAR_REC, TC_T);  // s_al[sa] written; s_al[sa] of chunk c - 2 read long ago
             const int q = c - cfirst;  // live chunk index
             double *yb = ybuf + (size_t)(q & 1) * TC_CH * TC_T;
-            if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), 2 * TC_T);  // the split group read chunk q - 2
+            if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), TC_NT);  // the split group read chunk q - 2
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const bool scaled = __any_sync(0xffffffffu, k < 0);
@@ -517,7 +520,8 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
                 for (int j = 16 * h; j < 16 * h + 16; ++j) {
                     // alpha x = alpha (1 - u) does not depend on y, so each step adds one DFMA
                     // (not two) to the dependency chain: one chain per SMSP is latency-bound
-                    const double ax = fma(-s_al[sa][j], u, s_al[sa][j]);
+                    const double a = __shfl_sync(0xffffffffu, al_cur, j);
+                    const double ax = fma(-a, u, a);
                     const double y = fma(ax, y1, -y2);
                     y2 = y1;
                     y1 = y;
@@ -529,15 +533,16 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
                     k += 1;
                 }
             }
-            if (q >= 0) bar_arrive(BAR_FULL + (q & 1), 2 * TC_T);
+            if (q >= 0) bar_arrive(BAR_FULL + (q & 1), TC_NT);
         }
     } else {
         // ------------------------------------------------ split / MMA group
         const uint32_t idesc = umma_idesc<N>();
         const int64_t chunk0 = A.chunk_base[m];
         const int Ey = A.Ey[m * A.nblk + blk];
+        constexpr int NS = TC_NT - TC_T;                 // split threads
         constexpr int BTOT = TcTile<N>::B_CHUNK / 16;   // uint4 of one chunk's B tiles
-        constexpr int BV = (BTOT + TC_T - 1) / TC_T;
+        constexpr int BV = (BTOT + NS - 1) / NS;
         for (int q = 0; q < nlive; ++q) {
             const int c = cfirst + q;
             const int st = q & 1;
@@ -547,106 +552,91 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
             const uint4 *bsrc = A.bdig + (chunk0 + c) * BTOT;
 #pragma unroll
             for (int i = 0; i < BV; ++i)
-                if (i * TC_T + r < BTOT) breg[i] = bsrc[i * TC_T + r];
+                if (i * NS + sp < BTOT) breg[i] = bsrc[i * NS + sp];
             // the MMAs of chunk q - 2 read this stage's tiles: wait (bounded) before rewriting them
             if (q >= 2 && ok && !mbar_wait(&mbar[st], (uint32_t)(((q >> 1) - 1) & 1))) ok = false;
-            bar_sync(BAR_FULL + st, 2 * TC_T);  // y of chunk q is in its stage
+            bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
             const double *yb = ybuf + (size_t)st * TC_CH * TC_T;
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
-                uint32_t pe[TC_S][4], po[TC_S][4];  // 8 even / 8 odd values per digit, bf16 pairs
+                uint32_t pk[TC_S][4];  // 8 values of this parity per digit, bf16 pairs
 #pragma unroll
-                for (int qq = 0; qq < 8; ++qq) {
-                    float de[TC_S], dd[TC_S];
-                    split_digits(yb[(16 * h + 2 * qq) * TC_T + r], Ey, de);
-                    split_digits(yb[(16 * h + 2 * qq + 1) * TC_T + r], Ey, dd);
+                for (int qq = 0; qq < 8; qq += 2) {
+                    float d0[TC_S], d1[TC_S];
+                    split_digits(yb[(16 * h + 2 * qq + par) * TC_T + r], Ey, d0);
+                    split_digits(yb[(16 * h + 2 * qq + 2 + par) * TC_T + r], Ey, d1);
                     // the digit floats are bf16-exact: a bf16 pair is the upper halves of two floats
-                    if ((qq & 1) == 0) {
 #pragma unroll
-                        for (int s = 0; s < TC_S; ++s) {
-                            pe[s][qq >> 1] = __float_as_uint(de[s]);
-                            po[s][qq >> 1] = __float_as_uint(dd[s]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int s = 0; s < TC_S; ++s) {
-                            pe[s][qq >> 1] = __byte_perm(pe[s][qq >> 1], __float_as_uint(de[s]), 0x7632);
-                            po[s][qq >> 1] = __byte_perm(po[s][qq >> 1], __float_as_uint(dd[s]), 0x7632);
-                        }
-                    }
+                    for (int s = 0; s < TC_S; ++s)
+                        pk[s][qq >> 1] = __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
                 }
-                if (h == 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, 2 * TC_T);  // y stage read
-                // k-group h of every A tile: core matrix (slot/8, h), row slot%8
+                if (h == 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TC_NT);  // y stage read
+                // k-group h of this parity's A tiles: core matrix (slot/8, h), row slot%8
                 const int off = ((h * 16) + (r >> 3)) * 128 + (r & 7) * 16;
 #pragma unroll
-                for (int s = 0; s < TC_S; ++s) {
-                    *(uint4 *)(a_st + (0 * TC_S + s) * TC_ATILE + off) = make_uint4(pe[s][0], pe[s][1], pe[s][2], pe[s][3]);
-                    *(uint4 *)(a_st + (1 * TC_S + s) * TC_ATILE + off) = make_uint4(po[s][0], po[s][1], po[s][2], po[s][3]);
-                }
+                for (int s = 0; s < TC_S; ++s)
+                    *(uint4 *)(a_st + (par * TC_S + s) * TC_ATILE + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
             }
 #pragma unroll
             for (int i = 0; i < BV; ++i)
-                if (i * TC_T + r < BTOT) ((uint4 *)b_st)[i * TC_T + r] = breg[i];
+                if (i * NS + sp < BTOT) ((uint4 *)b_st)[i * NS + sp] = breg[i];
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
-            ok = bar_red_and(BAR_SPLIT, TC_T, ok);
-            // lane 0 of each split warp issues the MMAs of one (parity, class group): warp 4 + 2 eo
-            // the classes below NACC - 1 (10 MMAs), warp 5 + 2 eo the merged last class (18); each
+            ok = bar_red_and(BAR_SPLIT, NS, ok);
+            // lane 0 of warps 4-7 issues the MMAs of one (parity, class group): warp 4 + 2 eo the
+            // classes below NACC - 1 (10 MMAs), warp 5 + 2 eo the merged last class (18); each
             // accumulator has one issuer, so its MMAs stay in order
-            if (ok && (r & 31) == 0) {
+            if (ok && lane == 0 && sp < 128) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
-                const int eo = r >> 6;
-                const bool last_group = ((r >> 5) & 1) != 0;
-                {
+                const int eo = sp >> 6;
+                const bool last_group = ((sp >> 5) & 1) != 0;
 #pragma unroll
-                    for (int w = 0; w <= TC_MAXW; ++w) {
-                        if ((w >= TcTile<N>::NACC - 1) != last_group) continue;
+                for (int w = 0; w <= TC_MAXW; ++w) {
+                    if ((w >= TcTile<N>::NACC - 1) != last_group) continue;
 #pragma unroll
-                        for (int i = 0; i <= w; ++i) {
-                            const int j = w - i;
-                            const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
-                            const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
-                            const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
-                            const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
-                            umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
-                        }
+                    for (int i = 0; i <= w; ++i) {
+                        const int j = w - i;
+                        const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
+                        const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
+                        const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
+                        const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
+                        umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
                     }
                 }
                 umma_commit(&mbar[st]);
             }
         }
-        // the last commit covers every MMA this thread issued: wait (bounded) before TMEM is read
+        // the last commits cover every MMA issued: wait (bounded) before TMEM is read
         if (ok && !mbar_wait(&mbar[(nlive - 1) & 1], (uint32_t)(((nlive - 1) >> 1) & 1))) ok = false;
-        ok = bar_red_and(BAR_SPLIT, TC_T, ok);
+        ok = bar_red_and(BAR_SPLIT, NS, ok);
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {
-            // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block
+            // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block; this thread
+            // takes columns [par N/2, (par + 1) N/2)
+            constexpr int NH = N / 2;
             const int lw = warp & 3;  // this warp may read lanes 32 lw .. 32 lw + 31
-            double acc[2][N];
+            double acc[2][NH];
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo)
 #pragma unroll
-                for (int n = 0; n < N; ++n) acc[eo][n] = 0.0;
+                for (int n = 0; n < NH; ++n) acc[eo][n] = 0.0;
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo) {
 #pragma unroll
                 for (int cls = 0; cls < TcTile<N>::NACC; ++cls) {
 #pragma unroll
-                    for (int n0 = 0; n0 < N; n0 += 16) {
-                        uint32_t v[16];
-                        const uint32_t addr =
-                            tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)((eo * TcTile<N>::NACC + cls) * N + n0);
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                            "[%16];"
-                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                              "=r"(v[14]), "=r"(v[15])
-                            : "r"(addr));
+                    for (int n0 = 0; n0 < NH; n0 += 8) {
+                        uint32_t v[8];
+                        const uint32_t addr = tmem + ((uint32_t)(lw * 32) << 16) +
+                                              (uint32_t)((eo * TcTile<N>::NACC + cls) * N + par * NH + n0);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                       "=r"(v[6]), "=r"(v[7])
+                                     : "r"(addr));
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) acc[eo][n0 + t] += (double)__uint_as_float(v[t]);
+                        for (int t = 0; t < 8; ++t) acc[eo][n0 + t] += (double)__uint_as_float(v[t]);
                     }
                 }
             }
@@ -654,19 +644,20 @@ __global__ void __launch_bounds__(2 * TC_T, 1) tc_synth_kernel(TcArgs A)
                 const int rn = A.slotN[slot], rs = A.slotS[slot];
                 const int64_t mstride = A.mmax + 1;
 #pragma unroll
-                for (int g = 0; g < N / 2; ++g) {
+                for (int gg = 0; gg < NH / 2; ++gg) {
+                    const int g = par * (NH / 2) + gg;  // map
                     if (g < A.nmaps) {
                         const double sr = pow2i_safe(Ey + A.Ea[m * N + 2 * g] - 12);
                         const double si = pow2i_safe(Ey + A.Ea[m * N + 2 * g + 1] - 12);
-                        const double er = acc[0][2 * g] * sr, ei = acc[0][2 * g + 1] * si;
-                        const double orr = acc[1][2 * g] * sr, oi = acc[1][2 * g + 1] * si;
+                        const double er = acc[0][2 * gg] * sr, ei = acc[0][2 * gg + 1] * si;
+                        const double orr = acc[1][2 * gg] * sr, oi = acc[1][2 * gg + 1] * si;
                         double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
                         if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
                         if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
                     }
                 }
             }
-        } else if (r == 0) {
+        } else if (sp == 0) {
             atomicOr(A.status, 1);
         }
     }
@@ -685,7 +676,7 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
     // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
     // and its accumulators take more than half of the tensor memory
     static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");
-    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), 2 * TC_T, TcWs<N>::SMEM, st>>>(A);
+    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT, TcWs<N>::SMEM, st>>>(A);
     return cudaGetLastError();
 }
 
