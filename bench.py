@@ -68,11 +68,13 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
+    ap.add_argument("--prec-anal", default="df", choices=["df", "tc"],
+                    help="precision-form analysis kernel: double-float (default) or tensor cores")
     return ap.parse_args()
 
 
-MODES = {"split": "precision form: FP64 recurrence, tensor-core (tcgen05, split-bf16) synthesis sum, "
-                  "double-float FP32 analysis sum",
+MODES = {"split": "precision form: FP64 recurrence, tensor-core (tcgen05, split-bf16, 7 digits) synthesis "
+                  "and analysis sums",
          "fp64": "plain FP64"}
 
 
@@ -259,6 +261,8 @@ def ours_arm(a, rank, world, local_rank):
         plan.alm2map(alm, out=mp)
         plan.map2alm(mp, out=alm_out)
 
+    plan.set_tuning(sht.TUNE_PREC_ANAL, 1 if a.prec_anal == "tc" else 0)
+
     def timed(mode, steps, warmup, sample_clocks):
         plan.set_mode(sht.MODE_SPLIT_BF16 if mode == "split" else sht.MODE_FP64)
         for _ in range(warmup):
@@ -306,7 +310,8 @@ def ours_arm(a, rank, world, local_rank):
 
     def split_roofline(run, steps):
         st = run["stages"]
-        if st["legendre_anal"][0] >= st["legendre_synth"][0]:
+        anal = st["legendre_anal"][0] >= st["legendre_synth"][0]
+        if anal and plan.tuning(sht.TUNE_PREC_ANAL) == 0:
             # double-float analysis on the FP32 pipe: per (l, m, ring-pair, map) two real products
             # (1 FMUL + 3 FFMA = 7 flops each) and their double-float sums (TwoSum + 2 adds = 8 flops)
             ms = st["legendre_anal"][0]
@@ -317,14 +322,25 @@ def ours_arm(a, rank, world, local_rank):
                     "traffic": traffic_from_profiles("legendre_anal_df_kernel"),
                     "peak_source": "derived: 128 FP32 FMA/clk/SM x %d SMs x %d MHz x 2 flop" % (nsm, SM_MAX_MHZ),
                     "work": "30 FP32 flops per (l, m, ring-pair, map): two double-float real products and sums"}
-        ms = st["legendre_synth"][0]
-        peak = MEASURED.get("bf16_tflops_sustained") or 1725.1
-        achieved = 42.0 * S * 2 * B * steps / (ms * 1e-3) / 1e12
-        return {"bound": "tensor", "pipe": "tcgen05 bf16", "kernel": "tc_synth_kernel", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_from_profiles("tc_synth_kernel"),
-                "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json)",
-                "work": "21 digit products x 2 flops per (l, m, ring-pair, real column)"}
+        # tensor-core kernels: bound by their FP64 recurrence (2 DFMA per (l, m, ring-pair) step,
+        # once per launch: 8 maps per analysis launch, 16 per synthesis launch); the contraction's
+        # useful tensor work is 28 digit products x 2 flops per step and real column (2 per map)
+        ms = st["legendre_anal"][0] if anal else st["legendre_synth"][0]
+        per = 8 if anal else 16
+        launches = -(-B // per)
+        achieved = 4.0 * S * launches * steps / (ms * 1e-3) / 1e12
+        tensor = 56.0 * S * 2 * B * steps / (ms * 1e-3) / 1e12
+        tpeak = MEASURED.get("bf16_tflops_sustained") or 1725.1
+        key = "tc_anal_kernel" if anal else "tc_synth_kernel"
+        return {"bound": "alu", "pipe": "fp64 (recurrence)", "kernel": key, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic_from_profiles(key),
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe %.3f "
+                               "TF/s" % (nsm, SM_MAX_MHZ, probe_tf),
+                "work": "4 FP64 flops per (l, m, ring-pair) step over the full triangle, once per launch "
+                        "(%d maps per launch)" % per,
+                "tensor": {"achieved": tensor, "peak": tpeak, "unit": "TFLOP/s", "frac": tensor / tpeak,
+                           "work": "28 bf16 digit products x 2 flops per (l, m, ring-pair) step and real column",
+                           "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json)"}}
 
     head = timed(a.mode, a.steps, a.warmup, True)
     total_ms, step_ms, stages, clk = head["total_ms"], head["step_ms"], head["stages"], head["clocks"]
@@ -455,7 +471,7 @@ def ours_arm(a, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64 recurrence; bf16 digits (tcgen05, f32 accum) + f32 double-float sums" if a.mode == "split"
+            "dtype": "f64 recurrence; bf16 digits (tcgen05, f32 accum, f64/double-float combination)" if a.mode == "split"
                      else "f64",
             "data": DATA,
             "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": L, "mmax": L,

@@ -26,13 +26,15 @@ def knobs_for(direction: str, mode: int) -> List[int]:
         # precision form: tensor-core groups, and the FP64 kernel on polar slot blocks
         return [sht.TUNE_TC_MAPS, sht.TUNE_SYNTH_MAPS] if mode == sht.MODE_SPLIT_BF16 else [sht.TUNE_SYNTH_MAPS]
     if direction == MAP2ALM:
-        return [sht.TUNE_DF_MAPS] if mode == sht.MODE_SPLIT_BF16 else [sht.TUNE_ANAL_MAPS, sht.TUNE_ANAL_SLOTS]
+        # precision form: tensor-core or double-float kernel (the latter's maps per launch)
+        return [sht.TUNE_PREC_ANAL, sht.TUNE_DF_MAPS] if mode == sht.MODE_SPLIT_BF16 else [sht.TUNE_ANAL_MAPS, sht.TUNE_ANAL_SLOTS]
     raise ValueError("unknown direction %r" % (direction,))
 
 
 def candidates(direction: str, mode: int, nmaps: int) -> List[Dict[int, int]]:
     """Knob settings worth timing: values above the call's map count act like the map count, so
-    only the smallest of those is kept."""
+    only the smallest of those is kept; the double-float maps per launch matter only when the
+    double-float analysis kernel is chosen."""
     ks = knobs_for(direction, mode)
     per_knob = []
     for k in ks:
@@ -41,7 +43,13 @@ def candidates(direction: str, mode: int, nmaps: int) -> List[Dict[int, int]]:
             keep = [v for v in vals if v < nmaps] + [min([v for v in vals if v >= nmaps] or [vals[-1]])]
             vals = sorted(set(keep))
         per_knob.append(vals)
-    return [dict(zip(ks, combo)) for combo in itertools.product(*per_knob)]
+    out = []
+    for combo in itertools.product(*per_knob):
+        c = dict(zip(ks, combo))
+        if c.get(sht.TUNE_PREC_ANAL) == 1 and c[sht.TUNE_DF_MAPS] != per_knob[ks.index(sht.TUNE_DF_MAPS)][-1]:
+            continue  # tensor-core analysis: the double-float grouping is unused, keep one setting
+        out.append(c)
+    return out
 
 
 def plan_key(plan, nmaps: int, direction: str) -> str:

@@ -606,7 +606,7 @@ cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, doub
 {
     *nlaunch = 0;
     if (p.mR < 0 || !p.polar_first_slot) return cudaSuccess;
-    if (slots != 2 * ANA_T) return cudaErrorInvalidValue;
+    if (slots != 2 * ANA_T && slots != ANA_T) return cudaErrorInvalidValue;
     AnaArgs A;
     A.slotN = p.d_slotN;
     A.slotS = p.d_slotS;
@@ -630,10 +630,16 @@ cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, doub
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = partial + (int64_t)g0 * p.nalm;
         if (nmaps - g0 >= 2) {
-            legendre_anal_kernel<2, 2><<<grid, ANA_T, 0, st>>>(A);
+            if (slots == ANA_T)
+                legendre_anal_kernel<2, 1><<<grid, ANA_T, 0, st>>>(A);
+            else
+                legendre_anal_kernel<2, 2><<<grid, ANA_T, 0, st>>>(A);
             g0 += 2;
         } else {
-            legendre_anal_kernel<1, 2><<<grid, ANA_T, 0, st>>>(A);
+            if (slots == ANA_T)
+                legendre_anal_kernel<1, 1><<<grid, ANA_T, 0, st>>>(A);
+            else
+                legendre_anal_kernel<1, 2><<<grid, ANA_T, 0, st>>>(A);
             g0 += 1;
         }
         ++*nlaunch;

@@ -333,6 +333,15 @@ cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
 
 }  // namespace
 
+cudaError_t launch_reduce_blocks_df(const float4 *partial, const double *cfac, double2 *alm, int nblk, int64_t nalm,
+                                    int nmaps, int lmax, int64_t blk_stride, int64_t fp64_lim, cudaStream_t st)
+{
+    const int64_t total = nalm * nmaps;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, cfac, alm, nblk, nalm, nmaps, lmax, blk_stride, fp64_lim);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_df_kernels()
 {
     cudaError_t e = configure_df<32>();

@@ -284,8 +284,9 @@ size_t synth_scratch_bytes(const Plan &p, int nmaps)
 
 size_t anal_partial_bytes(const Plan &p, int nmaps)
 {
-    return p.mode == SHT_MODE_SPLIT_BF16 ? sht::legendre_anal_df_partial_bytes(p, nmaps)
-                                         : sht::legendre_anal_partial_bytes(p, nmaps);
+    if (p.mode != SHT_MODE_SPLIT_BF16) return sht::legendre_anal_partial_bytes(p, nmaps);
+    return p.tune[SHT_TUNE_PREC_ANAL] ? sht::tc_anal_partial_bytes(p, nmaps)
+                                      : sht::legendre_anal_df_partial_bytes(p, nmaps);
 }
 
 sht_status run_ring_synth(Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps, cudaStream_t s)
@@ -312,10 +313,12 @@ sht_status run_legendre_anal(Plan &p, const double2 *delta, double2 *alm, double
                              cudaStream_t s)
 {
     if (p.mode == SHT_MODE_SPLIT_BF16) {
-        // precision form: double-float products and slot sums on the FP32 pipe (reduction included)
+        // precision form (reduction included): the l-sum contraction on the tensor cores, or
+        // double-float products and slot sums on the FP32 pipe
         StageScope sc(p, 3, s);
         int n = 0;
-        cudaError_t e = sht::launch_legendre_anal_df(p, delta, alm, partial, nmaps, s, &n);
+        cudaError_t e = p.tune[SHT_TUNE_PREC_ANAL] ? sht::launch_legendre_anal_tc(p, delta, alm, partial, nmaps, s, &n)
+                                                   : sht::launch_legendre_anal_df(p, delta, alm, partial, nmaps, s, &n);
         p.launches[3] += n;
         if (e != cudaSuccess) return cuda_fail(p, e, "legendre_anal");
         sc.done();
@@ -393,6 +396,7 @@ sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value)
     case SHT_TUNE_ANAL_SLOTS: ok = value == 1 || value == 4; break;
     case SHT_TUNE_DF_MAPS: ok = value == 4 || value == 8 || value == 16; break;
     case SHT_TUNE_TC_MAPS: ok = value == 8 || value == 16; break;
+    case SHT_TUNE_PREC_ANAL: ok = value == 0 || value == 1; break;
     default: ok = false;
     }
     if (!ok) return SHT_EINVAL;
@@ -417,6 +421,8 @@ sht_status sht_plan_set_mode(sht_plan_t plan, int mode)
     if (!plan || (mode != SHT_MODE_FP64 && mode != SHT_MODE_SPLIT_BF16)) return SHT_EINVAL;
     Plan &p = plan->p;
     if (mode == SHT_MODE_SPLIT_BF16) {
+        // only slot block 0 (128 slots) may be polar: its Reinsch CTAs run in FP64
+        if (p.nslots > 128 && p.slotTheta[128] > 0.0 && std::sin(p.slotTheta[128]) < 0.03) return SHT_EUNSUPPORTED;
         cudaError_t e = sht::build_tc_scales(p);  // one FP64 pass of the recurrence, synchronous
         if (e != cudaSuccess) return cuda_fail(p, e, "precision-form scales");
     }

@@ -15,7 +15,7 @@ class FakePlan:
         self.mode = mode
         self.nrings, self.npix = nrings, npix
         self.knobs = {sht.TUNE_SYNTH_MAPS: 4, sht.TUNE_ANAL_MAPS: 2, sht.TUNE_ANAL_SLOTS: 4,
-                      sht.TUNE_DF_MAPS: 8, sht.TUNE_TC_MAPS: 16}
+                      sht.TUNE_DF_MAPS: 8, sht.TUNE_TC_MAPS: 16, sht.TUNE_PREC_ANAL: 1}
 
     def set_tuning(self, k, v):
         assert v in sht.TUNE_VALUES[k]
@@ -28,14 +28,14 @@ class FakePlan:
 def test_candidates_cover_the_knobs_of_each_form():
     assert autotune.knobs_for(ALM2MAP, sht.MODE_FP64) == [sht.TUNE_SYNTH_MAPS]
     assert autotune.knobs_for(MAP2ALM, sht.MODE_FP64) == [sht.TUNE_ANAL_MAPS, sht.TUNE_ANAL_SLOTS]
-    assert autotune.knobs_for(MAP2ALM, sht.MODE_SPLIT_BF16) == [sht.TUNE_DF_MAPS]
+    assert autotune.knobs_for(MAP2ALM, sht.MODE_SPLIT_BF16) == [sht.TUNE_PREC_ANAL, sht.TUNE_DF_MAPS]
     c = autotune.candidates(ALM2MAP, sht.MODE_FP64, 16)
     assert [x[sht.TUNE_SYNTH_MAPS] for x in c] == [1, 2, 4]
     # values above the map count collapse to the smallest of them
     c = autotune.candidates(ALM2MAP, sht.MODE_FP64, 1)
     assert [x[sht.TUNE_SYNTH_MAPS] for x in c] == [1]
     c = autotune.candidates(MAP2ALM, sht.MODE_SPLIT_BF16, 6)
-    assert [x[sht.TUNE_DF_MAPS] for x in c] == [4, 8]
+    assert [(x[sht.TUNE_PREC_ANAL], x[sht.TUNE_DF_MAPS]) for x in c] == [(0, 4), (0, 8), (1, 8)]
     c = autotune.candidates(MAP2ALM, sht.MODE_FP64, 16)
     assert len(c) == 4 and {(x[sht.TUNE_ANAL_MAPS], x[sht.TUNE_ANAL_SLOTS]) for x in c} == {(1, 1), (1, 4), (2, 1), (2, 4)}
     assert len(autotune.candidates(ALM2MAP, sht.MODE_SPLIT_BF16, 16)) == 2 * 3

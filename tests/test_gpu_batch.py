@@ -96,7 +96,10 @@ def test_every_tuning_gives_the_same_result(mode):
             p.set_tuning(k, v)
         got = p.map2alm(s)
         if mode == sht.MODE_SPLIT_BF16:
-            assert torch.equal(got, ref_alm), cand
+            if cand[sht.TUNE_PREC_ANAL] == 0:      # double-float (the default): the same for every grouping
+                assert torch.equal(got, ref_alm), cand
+            else:                                   # tensor cores: within the precision bar
+                assert rel(got, ref_alm) < 1e-9, cand
         else:
             assert rel(got, ref_alm) < 1e-13, cand
     assert p.device_status() == 0
