@@ -162,7 +162,8 @@ typedef enum {
     SHT_TUNE_DF_MAPS = 3,    /* precision-form analysis: maps per launch, 4, 8 or 16 (default 8) */
     SHT_TUNE_TC_MAPS = 4,    /* precision-form synthesis: maps per tensor-core launch, 8 or 16 (default 16) */
     SHT_TUNE_PREC_ANAL = 5,  /* precision-form analysis kernel: 0 double-float FP32 (default), 1 tensor cores */
-    SHT_TUNE_COUNT = 6
+    SHT_TUNE_PREC_RING = 6,  /* precision-form ring DFTs: 1 double-float FP32 (default), 0 FP64 */
+    SHT_TUNE_COUNT = 7
 } sht_tune;
 sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value);
 int sht_plan_tuning(sht_plan_t plan, int knob); /* the knob's value; -1 for a null plan or unknown knob */

@@ -36,56 +36,146 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
 
+// ---------------------------------------------------------------- arithmetic of the ring DFTs
+//
+// The DFT code below is written once over an arithmetic P: complex values P::C, table entries
+// P::T, and the operations add, sub, mul (by a table entry or a value), conj and i-times.
+//   F64: double2, the plain form.
+//   DF:  a double-float complex (re hi, re lo, im hi, im lo) as float4, for the precision form.
+//        A real is hi + lo with |lo| <= ulp(hi) / 2 (renormalised after every operation): sums by
+//        TwoSum, products by an FMA two-product plus the cross terms, about 2^-44 relative.  On this
+//        part FP32 issues 64 times faster than FP64, so the DFTs run about 5x faster at an accuracy
+//        far inside the precision form's bar.  Inputs and outputs stay FP64.
+
+struct F64 {
+    using C = double2;
+    using T = double2;
+    static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
+    static __device__ __forceinline__ C sub(C a, C b) { return csub(a, b); }
+    static __device__ __forceinline__ C mul(C a, T b) { return cmul(a, b); }
+    static __device__ __forceinline__ C mulc(C a, C b) { return cmul(a, b); }
+    static __device__ __forceinline__ C conj(C a) { return conjd(a); }
+    static __device__ __forceinline__ C conjt(T a) { return conjd(a); }
+    static __device__ __forceinline__ C itimes(C a) { return make_double2(-a.y, a.x); }
+    static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+    static __device__ __forceinline__ C from(double2 v) { return v; }
+    static __device__ __forceinline__ C from_re_im(double re, double im) { return make_double2(re, im); }
+    static __device__ __forceinline__ double2 to(C v) { return v; }
+    static __device__ __forceinline__ double re(C v) { return v.x; }
+    static __device__ __forceinline__ double im(C v) { return v.y; }
+};
+
+// double-float helpers: a real is (hi, lo)
+__device__ __forceinline__ float2 dfn_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float v = s - a.x;
+    float e = (a.x - (s - v)) + (b.x - v);
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 dfn_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dfn_mul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+// FP64 -> (hi, lo): hi = v rounded to float, lo = v - hi rounded (exact split to 48 bits)
+__device__ __forceinline__ float2 dfn_from(double v)
+{
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double dfn_to(float2 a) { return (double)a.x + (double)a.y; }
+
+struct DF {
+    using C = float4;   // (re hi, re lo, im hi, im lo)
+    using T = float4;
+    static __device__ __forceinline__ float2 R(C a) { return make_float2(a.x, a.y); }
+    static __device__ __forceinline__ float2 I(C a) { return make_float2(a.z, a.w); }
+    static __device__ __forceinline__ C mk(float2 r, float2 i) { return make_float4(r.x, r.y, i.x, i.y); }
+    static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ C add(C a, C b) { return mk(dfn_add(R(a), R(b)), dfn_add(I(a), I(b))); }
+    static __device__ __forceinline__ C sub(C a, C b)
+    {
+        return mk(dfn_add(R(a), dfn_neg(R(b))), dfn_add(I(a), dfn_neg(I(b))));
+    }
+    static __device__ __forceinline__ C mulc(C a, C b)
+    {
+        const float2 re = dfn_add(dfn_mul(R(a), R(b)), dfn_neg(dfn_mul(I(a), I(b))));
+        const float2 im = dfn_add(dfn_mul(R(a), I(b)), dfn_mul(I(a), R(b)));
+        return mk(re, im);
+    }
+    static __device__ __forceinline__ C mul(C a, T b) { return mulc(a, b); }
+    static __device__ __forceinline__ C conj(C a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+    static __device__ __forceinline__ C conjt(T a) { return conj(a); }
+    static __device__ __forceinline__ C itimes(C a) { return make_float4(-a.z, -a.w, a.x, a.y); }
+    static __device__ __forceinline__ C half(C a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
+    static __device__ __forceinline__ C from(double2 v) { return mk(dfn_from(v.x), dfn_from(v.y)); }
+    static __device__ __forceinline__ C from_re_im(double re, double im) { return mk(dfn_from(re), dfn_from(im)); }
+    static __device__ __forceinline__ double2 to(C v) { return make_double2(dfn_to(R(v)), dfn_to(I(v))); }
+    static __device__ __forceinline__ double re(C v) { return dfn_to(R(v)); }
+    static __device__ __forceinline__ double im(C v) { return dfn_to(I(v)); }
+};
+
 // One Stockham pass: sub-transforms of length Lsub become length Lsub * p.
 // Input  X[j * (n / Lsub) + q],  j < Lsub, q < n / Lsub
 // Output Y[k * (n / (Lsub p)) + q'], k < Lsub p
-__device__ void stockham_pass(const double2 *__restrict__ X, double2 *__restrict__ Y, int n, int Lsub, int p,
-                              const double2 *__restrict__ tw)
+template <class P>
+__device__ void stockham_pass(const typename P::C *__restrict__ X, typename P::C *__restrict__ Y, int n, int Lsub,
+                              int p, const typename P::T *__restrict__ tw)
 {
+    using C = typename P::C;
     const int nq = n / (Lsub * p);
     const int nbf = Lsub * nq;
     const int inStride = n / Lsub;
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
         const int k1 = b / nq;
         const int q = b - k1 * nq;
-        const double2 *src = X + (int64_t)k1 * inStride + q;
-        double2 *dst = Y + (int64_t)k1 * nq + q;
+        const C *src = X + (int64_t)k1 * inStride + q;
+        C *dst = Y + (int64_t)k1 * nq + q;
         const int64_t ostride = (int64_t)Lsub * nq;
         if (p == 4) {
-            double2 a0 = src[0], a1 = src[nq], a2 = src[2 * nq], a3 = src[3 * nq];
+            C a0 = src[0], a1 = src[nq], a2 = src[2 * nq], a3 = src[3 * nq];
             if (k1) {
                 const int t = k1 * nq;
-                a1 = cmul(a1, tw[t]);
-                a2 = cmul(a2, tw[2 * t]);
-                a3 = cmul(a3, tw[3 * t]);
+                a1 = P::mul(a1, tw[t]);
+                a2 = P::mul(a2, tw[2 * t]);
+                a3 = P::mul(a3, tw[3 * t]);
             }
-            const double2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-            const double2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
-            const double2 id13 = make_double2(-d13.y, d13.x);  // i * (a1 - a3)
-            dst[0] = cadd(s02, s13);
-            dst[ostride] = cadd(d02, id13);
-            dst[2 * ostride] = csub(s02, s13);
-            dst[3 * ostride] = csub(d02, id13);
+            const C s02 = P::add(a0, a2), d02 = P::sub(a0, a2);
+            const C s13 = P::add(a1, a3), d13 = P::sub(a1, a3);
+            const C id13 = P::itimes(d13);  // i * (a1 - a3)
+            dst[0] = P::add(s02, s13);
+            dst[ostride] = P::add(d02, id13);
+            dst[2 * ostride] = P::sub(s02, s13);
+            dst[3 * ostride] = P::sub(d02, id13);
         } else if (p == 2) {
-            double2 a0 = src[0], a1 = src[nq];
-            if (k1) a1 = cmul(a1, tw[k1 * nq]);
-            dst[0] = cadd(a0, a1);
-            dst[ostride] = csub(a0, a1);
+            C a0 = src[0], a1 = src[nq];
+            if (k1) a1 = P::mul(a1, tw[k1 * nq]);
+            dst[0] = P::add(a0, a1);
+            dst[ostride] = P::sub(a0, a1);
         } else {
-            double2 a[MAXR];
+            C a[MAXR];
             a[0] = src[0];
             for (int r = 1; r < p; ++r) {
                 a[r] = src[(int64_t)r * nq];
-                if (k1) a[r] = cmul(a[r], tw[(int64_t)r * k1 * nq]);
+                if (k1) a[r] = P::mul(a[r], tw[(int64_t)r * k1 * nq]);
             }
             const int wstep = n / p;  // exp(2 pi i / p) = tw[n / p]
             for (int k2 = 0; k2 < p; ++k2) {
-                double2 acc = a[0];
+                C acc = a[0];
                 int e = 0;
                 for (int r = 1; r < p; ++r) {
                     e += k2;
                     if (e >= p) e -= p;
-                    acc = cadd(acc, cmul(a[r], tw[(int64_t)e * wstep]));
+                    acc = P::add(acc, P::mul(a[r], tw[(int64_t)e * wstep]));
                 }
                 dst[(int64_t)k2 * ostride] = acc;
             }
@@ -95,15 +185,18 @@ __device__ void stockham_pass(const double2 *__restrict__ X, double2 *__restrict
 
 // Length-n DFT with the + sign on B0[0, n) (all threads of the CTA).  Returns
 // the buffer that holds the result.  B1, B2 hold at least max(n, M) entries.
-__device__ double2 *cta_dft(const FftLen &F, const double2 *__restrict__ tab, double2 *B0, double2 *B1, double2 *B2)
+template <class P>
+__device__ typename P::C *cta_dft(const FftLen &F, const typename P::T *__restrict__ tab, typename P::C *B0,
+                                  typename P::C *B1, typename P::C *B2)
 {
+    using C = typename P::C;
     if (F.M == 0) {
-        double2 *X = B0, *Y = B1;
+        C *X = B0, *Y = B1;
         int Lsub = 1;
         for (int f = 0; f < F.nfac; ++f) {
             __syncthreads();
-            stockham_pass(X, Y, F.n, Lsub, F.fac[f], tab + F.tw);
-            double2 *t = X;
+            stockham_pass<P>(X, Y, F.n, Lsub, F.fac[f], tab + F.tw);
+            C *t = X;
             X = Y;
             Y = t;
             Lsub *= F.fac[f];
@@ -112,70 +205,73 @@ __device__ double2 *cta_dft(const FftLen &F, const double2 *__restrict__ tab, do
         return X;
     }
     const int n = F.n, M = F.M;
-    const double2 *ch = tab + F.chirp;
-    const double2 *filt = tab + F.filt;
-    for (int j = threadIdx.x; j < M; j += blockDim.x)
-        B1[j] = (j < n) ? cmul(B0[j], ch[j]) : make_double2(0.0, 0.0);
-    double2 *X = B1, *Y = B2;
+    const typename P::T *ch = tab + F.chirp;
+    const typename P::T *filt = tab + F.filt;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) B1[j] = (j < n) ? P::mul(B0[j], ch[j]) : P::zero();
+    C *X = B1, *Y = B2;
     int Lsub = 1;
     for (int f = 0; f < F.nfac; ++f) {
         __syncthreads();
-        stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
-        double2 *t = X;
+        stockham_pass<P>(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+        C *t = X;
         X = Y;
         Y = t;
         Lsub *= F.fac[f];
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < M; j += blockDim.x) X[j] = conjd(cmul(X[j], filt[j]));
+    for (int j = threadIdx.x; j < M; j += blockDim.x) X[j] = P::conj(P::mul(X[j], filt[j]));
     Lsub = 1;
     for (int f = 0; f < F.nfac; ++f) {
         __syncthreads();
-        stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
-        double2 *t = X;
+        stockham_pass<P>(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+        C *t = X;
         X = Y;
         Y = t;
         Lsub *= F.fac[f];
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) B0[k] = cmul(conjd(X[k]), ch[k]);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) B0[k] = P::mul(P::conj(X[k]), ch[k]);
     __syncthreads();
     return B0;
 }
 
+template <class P>
 struct RingArgs {
     const FftItem *items;
     const FftLen *lens;
-    const double2 *tab;
-    const double2 *phase;   // [nrings][mmax+1]
+    const typename P::T *tab;
+    const typename P::T *phase;   // [nrings][mmax+1]
     const int64_t *ofs;
     const double *w;
-    double2 *scratch;       // [grid][3][maxlen]
+    typename P::C *scratch;       // [grid][3][maxlen]
     int maxlen;
     int nitems, nmaps, nrings, mmax;
     int64_t npix;
-    const double2 *delta_in;   // synthesis input
-    double *map_out;           // synthesis output
-    const double *map_in;      // analysis input
-    double2 *delta_out;        // analysis output
+    const double2 *delta_in;      // synthesis input
+    double *map_out;              // synthesis output
+    const double *map_in;         // analysis input
+    double2 *delta_out;           // analysis output
 };
 
 // folded, phased spectrum bin k of one ring
-__device__ __forceinline__ double2 fold_bin(const double2 *__restrict__ d, const double2 *__restrict__ ph, int k, int n,
-                                            int mmax)
+template <class P>
+__device__ __forceinline__ typename P::C fold_bin(const double2 *__restrict__ d, const typename P::T *__restrict__ ph,
+                                                  int k, int n, int mmax)
 {
-    double2 c = make_double2(0.0, 0.0);
-    for (int m = k; m <= mmax; m += n) c = cadd(c, cmul(d[m], ph[m]));
+    typename P::C c = P::zero();
+    for (int m = k; m <= mmax; m += n) c = P::add(c, P::mul(P::from(d[m]), ph[m]));
     int m0 = (n - k) % n;
     if (m0 == 0) m0 = n;
-    for (int m = m0; m <= mmax; m += n) c = cadd(c, conjd(cmul(d[m], ph[m])));
+    for (int m = m0; m <= mmax; m += n) c = P::add(c, P::conj(P::mul(P::from(d[m]), ph[m])));
     return c;
 }
 
-__global__ void __launch_bounds__(FFT_T) ring_synth_kernel(RingArgs A)
+template <class P>
+__global__ void __launch_bounds__(FFT_T) ring_synth_kernel(RingArgs<P> A)
 {
-    double2 *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
-    double2 *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
+    using C = typename P::C;
+    C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
+    C *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
     const int64_t mstride = A.mmax + 1;
     const int nunits = A.nitems * A.nmaps;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -184,35 +280,37 @@ __global__ void __launch_bounds__(FFT_T) ring_synth_kernel(RingArgs A)
         const FftLen &F = A.lens[it.len_id];
         const int n = it.n;
         const double2 *dA = A.delta_in + ((int64_t)g * A.nrings + it.ringA) * mstride;
-        const double2 *pA = A.phase + (int64_t)it.ringA * mstride;
+        const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
         const double2 *dB = it.ringB >= 0 ? A.delta_in + ((int64_t)g * A.nrings + it.ringB) * mstride : nullptr;
-        const double2 *pB = it.ringB >= 0 ? A.phase + (int64_t)it.ringB * mstride : nullptr;
+        const typename P::T *pB = it.ringB >= 0 ? A.phase + (int64_t)it.ringB * mstride : nullptr;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const double2 ca = fold_bin(dA, pA, k, n, A.mmax);
-            double2 z = ca;
+            const C ca = fold_bin<P>(dA, pA, k, n, A.mmax);
+            C z = ca;
             if (dB) {
-                const double2 cb = fold_bin(dB, pB, k, n, A.mmax);
-                z = make_double2(ca.x - cb.y, ca.y + cb.x);  // C_A + i C_B
+                const C cb = fold_bin<P>(dB, pB, k, n, A.mmax);
+                z = P::add(ca, P::itimes(cb));  // C_A + i C_B
             }
             B0[k] = z;
         }
         __syncthreads();
-        const double2 *X = cta_dft(F, A.tab, B0, B1, B2);
+        const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);
         double *outA = A.map_out + (int64_t)g * A.npix + A.ofs[it.ringA];
         double *outB = it.ringB >= 0 ? A.map_out + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double2 z = X[j];
-            outA[j] = z.x;
-            if (outB) outB[j] = z.y;
+            const C z = X[j];
+            outA[j] = P::re(z);
+            if (outB) outB[j] = P::im(z);
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(FFT_T) ring_anal_kernel(RingArgs A)
+template <class P>
+__global__ void __launch_bounds__(FFT_T) ring_anal_kernel(RingArgs<P> A)
 {
-    double2 *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
-    double2 *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
+    using C = typename P::C;
+    C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
+    C *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
     const int64_t mstride = A.mmax + 1;
     const int nunits = A.nitems * A.nmaps;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
@@ -223,37 +321,47 @@ __global__ void __launch_bounds__(FFT_T) ring_anal_kernel(RingArgs A)
         const double *sA = A.map_in + (int64_t)g * A.npix + A.ofs[it.ringA];
         const double *sB = it.ringB >= 0 ? A.map_in + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
         for (int j = threadIdx.x; j < n; j += blockDim.x)
-            B0[j] = make_double2(sA[j], sB ? -sB[j] : 0.0);  // conj(s_A + i s_B)
+            B0[j] = P::from_re_im(sA[j], sB ? -sB[j] : 0.0);  // conj(s_A + i s_B)
         __syncthreads();
-        const double2 *X = cta_dft(F, A.tab, B0, B1, B2);  // conj(S)
-        const double2 *pA = A.phase + (int64_t)it.ringA * mstride;
+        const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);  // conj(S)
+        const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
         double2 *oA = A.delta_out + ((int64_t)g * A.nrings + it.ringA) * mstride;
         const double wA = A.w[it.ringA];
         if (it.ringB < 0) {
             for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
-                const double2 S = conjd(X[m % n]);
-                const double2 v = cmul(conjd(pA[m]), S);
+                const C S = P::conj(X[m % n]);
+                const double2 v = P::to(P::mulc(P::conjt(pA[m]), S));
                 oA[m] = make_double2(wA * v.x, m == 0 ? 0.0 : wA * v.y);
             }
         } else {
-            const double2 *pB = A.phase + (int64_t)it.ringB * mstride;
+            const typename P::T *pB = A.phase + (int64_t)it.ringB * mstride;
             double2 *oB = A.delta_out + ((int64_t)g * A.nrings + it.ringB) * mstride;
             const double wB = A.w[it.ringB];
             for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
                 const int k = m % n;
                 const int kc = (n - k) % n;
-                const double2 S = conjd(X[k]);
-                const double2 Sc = X[kc];  // conj(S_{-k})
-                const double2 SA = make_double2(0.5 * (S.x + Sc.x), 0.5 * (S.y + Sc.y));
-                const double2 D = csub(S, Sc);
-                const double2 SB = make_double2(0.5 * D.y, -0.5 * D.x);  // D / (2 i)
-                const double2 va = cmul(conjd(pA[m]), SA);
-                const double2 vb = cmul(conjd(pB[m]), SB);
+                const C S = P::conj(X[k]);
+                const C Sc = X[kc];  // conj(S_{-k})
+                const C SA = P::half(P::add(S, Sc));
+                const C D = P::half(P::sub(S, Sc));
+                const C SB = P::conj(P::itimes(P::conj(D)));  // D / (2 i) with D halved: -i D
+                const double2 va = P::to(P::mulc(P::conjt(pA[m]), SA));
+                const double2 vb = P::to(P::mulc(P::conjt(pB[m]), SB));
                 oA[m] = make_double2(wA * va.x, m == 0 ? 0.0 : wA * va.y);
                 oB[m] = make_double2(wB * vb.x, m == 0 ? 0.0 : wB * vb.y);
             }
         }
         __syncthreads();
+    }
+}
+
+// double-float copies of FP64 tables (hi = rounded, lo = remainder rounded)
+__global__ void df_table_kernel(const double2 *__restrict__ src, float4 *__restrict__ dst, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = src[t];
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        dst[t] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
     }
 }
 
@@ -305,7 +413,7 @@ __global__ void __launch_bounds__(FFT_T) bluestein_filter_kernel(const FftLen *l
         int Lsub = 1;
         for (int f = 0; f < F.nfac; ++f) {
             __syncthreads();
-            stockham_pass(X, Y, M, Lsub, F.fac[f], tab + F.tw);
+            stockham_pass<F64>(X, Y, M, Lsub, F.fac[f], tab + F.tw);
             double2 *tmp = X;
             X = Y;
             Y = tmp;
@@ -369,75 +477,97 @@ size_t ring_scratch_bytes(const Plan &p) { return (size_t)ring_grid(p) * 3 * (si
 
 int ring_grid(const Plan &p) { return std::max(1, std::min(p.nitems, 2 * 152)); }
 
-cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
-                              cudaStream_t st)
+namespace {
+
+bool ring_df(const Plan &p) { return p.mode == SHT_MODE_SPLIT_BF16 && p.tune[SHT_TUNE_PREC_RING] && p.d_fft_tab_df; }
+
+template <class P>
+RingArgs<P> ring_args(const Plan &p, const typename P::T *tab, const typename P::T *phase, void *scratch, int nmaps)
 {
-    RingArgs A{};
+    RingArgs<P> A{};
     A.items = p.d_items;
     A.lens = p.d_lens;
-    A.tab = p.d_fft_tab;
-    A.phase = p.d_phase;
+    A.tab = tab;
+    A.phase = phase;
     A.ofs = p.d_ofs;
     A.w = p.d_w;
-    A.scratch = scratch;
+    A.scratch = (typename P::C *)scratch;
     A.maxlen = p.fft_maxlen;
     A.nitems = p.nitems;
     A.nmaps = nmaps;
     A.nrings = p.nrings;
     A.mmax = p.mmax;
     A.npix = p.npix;
-    A.delta_in = delta;
-    A.map_out = map;
-    ring_synth_kernel<<<ring_grid(p), FFT_T, 0, st>>>(A);
-    return cudaGetLastError();
+    return A;
 }
 
-// Same as launch_ring_synth with a caller-chosen persistent grid (the scratch
-// holds 3 * fft_maxlen complex entries per CTA).
+}  // namespace
+
+// The ring stages run in double-float arithmetic in the precision form (unless SHT_TUNE_PREC_RING
+// is 0), in FP64 otherwise.
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st)
 {
-    RingArgs A{};
-    A.items = p.d_items;
-    A.lens = p.d_lens;
-    A.tab = p.d_fft_tab;
-    A.phase = p.d_phase;
-    A.ofs = p.d_ofs;
-    A.w = p.d_w;
-    A.scratch = scratch;
-    A.maxlen = p.fft_maxlen;
-    A.nitems = p.nitems;
-    A.nmaps = nmaps;
-    A.nrings = p.nrings;
-    A.mmax = p.mmax;
-    A.npix = p.npix;
-    A.delta_in = delta;
-    A.map_out = map;
-    ring_synth_kernel<<<grid, FFT_T, 0, st>>>(A);
+    if (ring_df(p)) {
+        RingArgs<DF> A = ring_args<DF>(p, p.d_fft_tab_df, p.d_phase_df, scratch, nmaps);
+        A.delta_in = delta;
+        A.map_out = map;
+        ring_synth_kernel<DF><<<grid, FFT_T, 0, st>>>(A);
+    } else {
+        RingArgs<F64> A = ring_args<F64>(p, p.d_fft_tab, p.d_phase, scratch, nmaps);
+        A.delta_in = delta;
+        A.map_out = map;
+        ring_synth_kernel<F64><<<grid, FFT_T, 0, st>>>(A);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
+                              cudaStream_t st)
+{
+    return launch_ring_synth_grid(p, delta, map, scratch, nmaps, ring_grid(p), st);
 }
 
 cudaError_t launch_ring_anal(const Plan &p, const double *map, double2 *delta, double2 *scratch, int nmaps,
                              cudaStream_t st)
 {
-    RingArgs A{};
-    A.items = p.d_items;
-    A.lens = p.d_lens;
-    A.tab = p.d_fft_tab;
-    A.phase = p.d_phase;
-    A.ofs = p.d_ofs;
-    A.w = p.d_w;
-    A.scratch = scratch;
-    A.maxlen = p.fft_maxlen;
-    A.nitems = p.nitems;
-    A.nmaps = nmaps;
-    A.nrings = p.nrings;
-    A.mmax = p.mmax;
-    A.npix = p.npix;
-    A.map_in = map;
-    A.delta_out = delta;
-    ring_anal_kernel<<<ring_grid(p), FFT_T, 0, st>>>(A);
+    if (ring_df(p)) {
+        RingArgs<DF> A = ring_args<DF>(p, p.d_fft_tab_df, p.d_phase_df, scratch, nmaps);
+        A.map_in = map;
+        A.delta_out = delta;
+        ring_anal_kernel<DF><<<ring_grid(p), FFT_T, 0, st>>>(A);
+    } else {
+        RingArgs<F64> A = ring_args<F64>(p, p.d_fft_tab, p.d_phase, scratch, nmaps);
+        A.map_in = map;
+        A.delta_out = delta;
+        ring_anal_kernel<F64><<<ring_grid(p), FFT_T, 0, st>>>(A);
+    }
     return cudaGetLastError();
+}
+
+// double-float copies of the DFT and phase tables for the precision form (synchronous, once)
+cudaError_t build_df_ring_tables(Plan &p)
+{
+    if (p.d_fft_tab_df) return cudaSuccess;
+    const int64_t nph = (int64_t)p.nrings * (p.mmax + 1);
+    const int64_t ntab = std::max<int64_t>(p.fft_tab_len, 1);
+    float4 *tab = nullptr, *ph = nullptr;
+    cudaError_t e = cudaMalloc(&tab, sizeof(float4) * ntab);
+    if (e == cudaSuccess) e = cudaMalloc(&ph, sizeof(float4) * nph);
+    if (e == cudaSuccess) {
+        df_table_kernel<<<152 * 8, 256>>>(p.d_fft_tab, tab, p.fft_tab_len);
+        df_table_kernel<<<152 * 8, 256>>>(p.d_phase, ph, nph);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(tab);
+        cudaFree(ph);
+        return e;
+    }
+    p.d_fft_tab_df = tab;
+    p.d_phase_df = ph;
+    return cudaSuccess;
 }
 
 cudaError_t build_phase_table(Plan &p)

@@ -65,6 +65,8 @@ struct Plan {
     FftLen *d_lens = nullptr;
     std::vector<FftLen> lens;
     double2 *d_fft_tab = nullptr;
+    float4 *d_fft_tab_df = nullptr;     // double-float copies for the precision form (built by set_mode)
+    float4 *d_phase_df = nullptr;
     int64_t fft_tab_len = 0;
     int fft_maxlen = 0;         // per-CTA scratch length (complex entries, per buffer)
 
@@ -78,7 +80,7 @@ struct Plan {
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
     // launch tuning (sht_tune): maps or slots per thread per launch
-    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 0};
+    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 0, 1};
 
     // workspace, grown on demand
     void *d_ws = nullptr;
@@ -108,6 +110,7 @@ cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *
 int legendre_anal_nblk(const Plan &p);
 int legendre_anal_default_slots(const Plan &p);  // default SHT_TUNE_ANAL_SLOTS for the plan's slot count
 cudaError_t configure_tc_kernels();              // one-time function attributes (not stream work)
+cudaError_t build_df_ring_tables(Plan &p);       // double-float DFT and phase tables (precision form)
 cudaError_t configure_df_kernels();
 size_t legendre_anal_partial_bytes(const Plan &p, int nmaps);
 cudaError_t launch_ring_synth(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,

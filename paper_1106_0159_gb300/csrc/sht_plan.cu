@@ -27,7 +27,7 @@ void free_plan_device(Plan &p)
 {
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
                     p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
-                    p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status};
+                    p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -44,6 +44,8 @@ void free_plan_device(Plan &p)
     p.d_tc_chunk_m = nullptr;
     p.d_tc_Ey = nullptr;
     p.d_status = nullptr;
+    p.d_fft_tab_df = nullptr;
+    p.d_phase_df = nullptr;
     p.ws_bytes = 0;
 }
 
@@ -397,6 +399,7 @@ sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value)
     case SHT_TUNE_DF_MAPS: ok = value == 4 || value == 8 || value == 16; break;
     case SHT_TUNE_TC_MAPS: ok = value == 8 || value == 16; break;
     case SHT_TUNE_PREC_ANAL: ok = value == 0 || value == 1; break;
+    case SHT_TUNE_PREC_RING: ok = value == 0 || value == 1; break;
     default: ok = false;
     }
     if (!ok) return SHT_EINVAL;
@@ -424,7 +427,8 @@ sht_status sht_plan_set_mode(sht_plan_t plan, int mode)
         // only slot block 0 (128 slots) may be polar: its Reinsch CTAs run in FP64
         if (p.nslots > 128 && p.slotTheta[128] > 0.0 && std::sin(p.slotTheta[128]) < 0.03) return SHT_EUNSUPPORTED;
         cudaError_t e = sht::build_tc_scales(p);  // one FP64 pass of the recurrence, synchronous
-        if (e != cudaSuccess) return cuda_fail(p, e, "precision-form scales");
+        if (e == cudaSuccess) e = sht::build_df_ring_tables(p);
+        if (e != cudaSuccess) return cuda_fail(p, e, "precision-form tables");
     }
     p.mode = mode;
     return SHT_OK;

@@ -161,3 +161,29 @@ def test_split_analysis_full_size_sampled(nside, L, kernel):
         refs = oracle.map2alm_ms(geom, s[g], L, ms)
         got = np.concatenate([b[g][oracle.alm_index(L, mm, mm):oracle.alm_index(L, mm, mm) + L - mm + 1] for mm in ms])
         assert rel(got, np.concatenate(refs)) < TOL_TC
+
+
+# ---------------------------------------------------------------- ring DFTs in the precision form
+# (double-float arithmetic on the FP32 pipe; ~2^-44 relative, far inside the bar)
+
+@pytest.mark.parametrize("grid", ["healpix", "gl"])
+def test_split_ring_stages_match_fp64(grid):
+    from paper_1106_0159_gb300 import sht
+    if grid == "healpix":
+        geom, L = geometry.healpix(512), 1024     # cap rings of every length 4i: Bluestein and Stockham
+    else:
+        geom, L = geometry.gauss_legendre(257, 513), 256
+    p = _plan(geom, L)
+    q = _plain(geom, L)
+    R = len(geom[0])
+    d = dev(inputs.random_delta(R, L, seed=81, nmaps=3))
+    s = dev(inputs.white_map(geometry.npix(geom), seed=82, nmaps=3))
+    m_split, m_64 = host(p.ring_synth(d)), host(q.ring_synth(d))
+    d_split, d_64 = host(p.ring_anal(s)), host(q.ring_anal(s))
+    assert p.device_status() == 0
+    for g in range(3):
+        assert rel(m_split[g], m_64[g]) < 1e-12, g
+        assert rel(d_split[g], d_64[g]) < 1e-12, g
+    # the FP64 ring DFTs are still there when the knob asks for them
+    p.set_tuning(sht.TUNE_PREC_RING, 0)
+    assert np.array_equal(host(p.ring_synth(d)), m_64)
