@@ -32,7 +32,11 @@ namespace {
 
 constexpr int DF_T = 256;          // threads = slots per CTA
 constexpr int DF_CHL = 32;         // l per shared-memory chunk (multiple of 8)
-constexpr int DF_G = 8;            // l per reduce-scatter round
+#ifndef DF_G_L
+#define DF_G_L 8
+#endif
+constexpr int DF_G = DF_G_L;       // l per reduce-scatter round: 8 (16: fewer instructions, but 702 vs 677 ms at lmax 4096)
+static_assert(DF_G == 8 || DF_G == 16, "DF_G is 8 or 16");
 // Maps per launch: SHT_TUNE_DF_MAPS (16, 8 or 4; default 8).  Fewer maps: less shared memory and
 // more CTAs per SM, but the FP64 recurrence runs once per launch.  lmax = 4096, HEALPix 2048, 16 maps
 // on GB300: 16 maps per launch 809 ms, 8 maps 677 ms (two CTAs of 8 warps per SM), 4 maps 781 ms.
@@ -125,10 +129,10 @@ __device__ __forceinline__ float2 shfl_xor_df(float2 v, int m)
 }
 
 // Reduce-scatter of DF_G double-float values per lane over the warp: every lane ends with the
-// warp total of value (lane & (DF_G - 1)).  The caller stores value i at v[i ^ (lane & 7)], so
+// warp total of value (lane & (DF_G - 1)).  The caller stores value i at v[i ^ (lane & (DF_G - 1))], so
 // that in every halving round the value a lane keeps and the one it sends sit in fixed
 // registers (no per-lane selects): after the round with partner lane ^ h, v[i] (i < h) holds
-// both lanes' sums of value i ^ (lane & 7).
+// both lanes' sums of value i ^ (lane & (DF_G - 1)).
 __device__ __forceinline__ float2 warp_reduce_scatter_df(float2 v[DF_G])
 {
 #pragma unroll
@@ -137,16 +141,16 @@ __device__ __forceinline__ float2 warp_reduce_scatter_df(float2 v[DF_G])
         for (int i = 0; i < h; ++i) v[i] = df_add(v[i], shfl_xor_df(v[i + h], h));
     }
     float2 r = v[0];
-    r = df_add(r, shfl_xor_df(r, 8));
-    r = df_add(r, shfl_xor_df(r, 16));
+#pragma unroll
+    for (int o = DF_G; o < 32; o <<= 1) r = df_add(r, shfl_xor_df(r, o));  // the other lane groups
     return r;
 }
 
-// v[i] <- v[i ^ b] for b = lane & 7 (three conditional swaps)
+// v[i] <- v[i ^ b] for b = lane & (DF_G - 1) (log2 DF_G conditional swaps)
 __device__ __forceinline__ void xor_permute(float2 v[DF_G], int b)
 {
 #pragma unroll
-    for (int h = 4; h >= 1; h >>= 1) {
+    for (int h = DF_G / 2; h >= 1; h >>= 1) {
         const bool sw = (b & h) != 0;
 #pragma unroll
         for (int i = 0; i < DF_G; ++i) {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
                 yv[jj] = use ? d2df(y) : make_float2(0.f, 0.f);
                 live |= use;
             }
-            if (((j0 + 8) & 15) == 0 && scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+            if (((j0 + DF_G) & 15) == 0 && scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
                 y1 *= 0x1p-512;
                 y2 *= 0x1p-512;
                 k += 1;
