@@ -76,6 +76,8 @@ struct Plan {
     int64_t *d_tc_chunk_base = nullptr; // [mmax + 1]
     int *d_tc_chunk_m = nullptr;        // [tc_total_chunks]
     int *d_tc_Ey = nullptr;             // [2][mmax + 1][slot blocks]: scale exponent of y = lambda / c, first live chunk
+    double2 *d_tc_ck_y = nullptr;       // [mmax + 1][slot blocks][128] recurrence state at the first live chunk & ~1
+    int *d_tc_ck_k = nullptr;           // its rescaling exponents
     int *d_status = nullptr;            // device status word (bounded waits that gave up)
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 

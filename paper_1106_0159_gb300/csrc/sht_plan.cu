@@ -27,7 +27,8 @@ void free_plan_device(Plan &p)
 {
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
                     p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
-                    p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df};
+                    p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df,
+                    p.d_tc_ck_y, p.d_tc_ck_k};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -46,6 +47,8 @@ void free_plan_device(Plan &p)
     p.d_status = nullptr;
     p.d_fft_tab_df = nullptr;
     p.d_phase_df = nullptr;
+    p.d_tc_ck_y = nullptr;
+    p.d_tc_ck_k = nullptr;
     p.ws_bytes = 0;
 }
 
