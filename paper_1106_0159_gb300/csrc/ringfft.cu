@@ -25,7 +25,16 @@
 namespace sht {
 namespace {
 
-constexpr int FFT_T = 256;
+// Launch shape of the ring kernels: RING_CTAS_PER_SM x 152 persistent CTAs of RING_T threads.
+// lmax 4096, HEALPix 2048, 16 maps, double-float DFTs (synthesis / analysis ms): 2 x 256: 57 / 47,
+// 1 x 256: 80 / 62, 1 x 512: 58 / 49, 2 x 512: 47 / 39 (more threads per DFT, same scratch).
+#ifndef RING_T
+#define RING_T 512
+#endif
+#ifndef RING_CTAS_PER_SM
+#define RING_CTAS_PER_SM 2
+#endif
+constexpr int FFT_T = RING_T;
 constexpr int MAXR = 13;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
@@ -86,13 +95,39 @@ __device__ __forceinline__ float2 dfn_mul(float2 a, float2 b)
     const float h = p + e;
     return make_float2(h, e - (h - p));
 }
-// FP64 -> (hi, lo): hi = v rounded to float, lo = v - hi rounded (exact split to 48 bits)
+// FP64 -> (hi, lo) from the bit pattern, on the integer pipe (an FP64 <-> FP32 conversion takes an
+// FP64 issue slot): hi = sign, exponent and the top 23 fraction bits; lo = the remaining 29 bits,
+// rounded to 24.  Below 2^-74 the remainder would leave the FP32 range: those (rare) values take
+// the conversion instructions, and values below 2^-126 flush to zero.
 __device__ __forceinline__ float2 dfn_from(double v)
 {
-    const float h = __double2float_rn(v);
-    return make_float2(h, __double2float_rn(v - (double)h));
+    const int hiw = __double2hiint(v);
+    const unsigned low = (unsigned)__double2loint(v);
+    const int ex = (hiw >> 20) & 0x7ff;
+    const int e = ex - 1023;
+    if (ex == 0 || e < -126) return make_float2(0.f, 0.f);
+    if (e < 52 - 126) {
+        const float h = __double2float_rn(v);
+        return make_float2(h, __double2float_rn(v - (double)h));
+    }
+    const unsigned sign = (unsigned)hiw & 0x80000000u;
+    const unsigned frac23 = (((unsigned)hiw & 0xFFFFFu) << 3) | (low >> 29);
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | frac23);
+    const unsigned rem = low & 0x1FFFFFFFu;
+    const float sc = (e - 52 >= -126) ? __uint_as_float((unsigned)(e - 52 + 127) << 23) : 0.f;
+    const float lo = (float)rem * sc;
+    return make_float2(hi, sign ? -lo : lo);
 }
-__device__ __forceinline__ double dfn_to(float2 a) { return (double)a.x + (double)a.y; }
+// float -> double from the bit pattern (normal floats and zero, the only ones produced here)
+__device__ __forceinline__ double dfn_widen(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    if (ex == 0) return 0.0;
+    const unsigned hi = (b & 0x80000000u) | ((ex + (1023 - 127)) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double dfn_to(float2 a) { return dfn_widen(a.x) + dfn_widen(a.y); }
 
 struct DF {
     using C = float4;   // (re hi, re lo, im hi, im lo)
@@ -475,7 +510,7 @@ bool factor_smooth(int n, std::vector<int> &fac)
 
 size_t ring_scratch_bytes(const Plan &p) { return (size_t)ring_grid(p) * 3 * (size_t)p.fft_maxlen * sizeof(double2); }
 
-int ring_grid(const Plan &p) { return std::max(1, std::min(p.nitems, 2 * 152)); }
+int ring_grid(const Plan &p) { return std::max(1, std::min(p.nitems, RING_CTAS_PER_SM * 152)); }
 
 namespace {
 
