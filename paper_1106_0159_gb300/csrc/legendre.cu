@@ -629,7 +629,13 @@ cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, doub
     for (int g0 = 0; g0 < nmaps;) {
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = partial + (int64_t)g0 * p.nalm;
-        if (nmaps - g0 >= 2) {
+        if (nmaps - g0 >= 4) {  // the Reinsch recurrence (4 DFMA per step) runs once per launch
+            if (slots == ANA_T)
+                legendre_anal_kernel<4, 1><<<grid, ANA_T, 0, st>>>(A);
+            else
+                legendre_anal_kernel<4, 2><<<grid, ANA_T, 0, st>>>(A);
+            g0 += 4;
+        } else if (nmaps - g0 >= 2) {
             if (slots == ANA_T)
                 legendre_anal_kernel<2, 1><<<grid, ANA_T, 0, st>>>(A);
             else

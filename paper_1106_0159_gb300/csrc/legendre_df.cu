@@ -292,8 +292,13 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
     }
 }
 
-// a_lm = c_lm * sum over blocks of (hi + lo) in FP64.  Block 0 holds FP64 partials (double2,
-// from the Reinsch kernel) for the indices below fp64_lim, i.e. for m <= mR of a polar plan.
+// a_lm = c_lm * sum over blocks of (hi + lo).  The blocks are added in order as double-float
+// pairs on the FP32 pipe (widening each partial to FP64 and adding there made this kernel
+// FP64-bound: four conversions and four adds per complex value and block) and the sum is widened
+// once.  Block 0 holds FP64 partials (double2, from the Reinsch kernel) for the indices below
+// fp64_lim, i.e. for m <= mR of a polar plan; they enter the sum split into hi + lo.
+__device__ __forceinline__ double widen_df(float2 a) { return (double)a.x + (double)a.y; }
+
 __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double *__restrict__ cfac,
                                         double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
                                         int64_t blk_stride, int64_t fp64_lim)
@@ -301,20 +306,27 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
     const int64_t total = nalm * nmaps;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = t / nalm, i = t - g * nalm;
-        double re = 0.0, im = 0.0;
-        for (int bk = 0; bk < nblk; ++bk) {
-            const float4 v = partial[bk * blk_stride + g * nalm + i];
-            if (bk == 0 && i < fp64_lim) {
+        const float4 *src = partial + g * nalm + i;
+        float2 re, im;
+        {
+            const float4 v = src[0];
+            if (i < fp64_lim) {
                 const double2 d = *reinterpret_cast<const double2 *>(&v);
-                re += d.x;
-                im += d.y;
+                re = d2df(d.x);
+                im = d2df(d.y);
             } else {
-                re += (double)v.x + (double)v.y;
-                im += (double)v.z + (double)v.w;
+                re = make_float2(v.x, v.y);
+                im = make_float2(v.z, v.w);
             }
         }
+#pragma unroll 4
+        for (int bk = 1; bk < nblk; ++bk) {
+            const float4 v = src[(int64_t)bk * blk_stride];
+            re = df_add(re, make_float2(v.x, v.y));
+            im = df_add(im, make_float2(v.z, v.w));
+        }
         const double c = cfac[i];
-        alm[t] = make_double2(c * re, i <= lmax ? 0.0 : c * im);
+        alm[t] = make_double2(c * widen_df(re), i <= lmax ? 0.0 : c * widen_df(im));
     }
 }
 
