@@ -652,7 +652,7 @@ def serve_leg(a, rep, local_rank):
             st = srv.stats()
             st["clocks"] = clocks.stop()
             out[name] = st
-        out["device_status"] = max(be.plan(k, s).device_status() for k in keys for s in range(nstreams))
+        out["device_status"] = max(be.plan(k).device_status() for k in keys)
         be.close()
         return out
 

@@ -96,9 +96,18 @@ int        sht_plan_mode(sht_plan_t plan);
 /*
  * Device status word of the plan: bit 0 is set when a bounded wait inside a tensor-core kernel
  * gave up (the kernel then wrote no output for that block and released its resources).
- * Copies the word to *status (synchronous); clear != 0 resets it.
+ * Copies the word to *status (synchronous, after the device finishes its work); clear != 0 resets
+ * it.  Returns SHT_ETIMEOUT while bit 0 is set (read before the clear), SHT_OK otherwise.
  */
 sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear);
+
+/*
+ * Failure-path self test (no counterpart in the paper): enqueues on `stream` a one-block kernel
+ * that waits, with a short poll budget, on an mbarrier nobody arrives at, the way the tensor-core
+ * kernels wait for their MMAs; when the budget runs out it sets bit 0 of the plan's status word
+ * and returns.  sht_plan_device_status then reports SHT_ETIMEOUT.  The GPU context stays usable.
+ */
+sht_status sht_plan_selftest_timeout(sht_plan_t plan, void *stream);
 
 /* Free the plan, its device tables and workspace (synchronises the device). NULL is ignored. */
 void sht_plan_destroy(sht_plan_t plan);
@@ -117,6 +126,20 @@ sht_status sht_alm2map(sht_plan_t plan, const void *alm, double *map, int nmaps,
  * blocks (deterministic: no atomics).
  */
 sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream);
+
+/*
+ * The transforms on caller-owned scratch (no counterpart in the paper): the same as sht_alm2map /
+ * sht_map2alm, with the plan's own scratch replaced by `scratch` (device memory of at least
+ * sht_workspace_bytes(plan, nmaps) bytes, 256-byte aligned, not shared with a call still in
+ * flight).  One plan can then serve several streams at once, each with its own scratch: the
+ * plan's tables are only read.  Calls on one plan must come from one host thread (the plan's
+ * launch counters and stage timing are host state).  SHT_EINVAL for a missing, misaligned or too
+ * small scratch, otherwise as sht_alm2map / sht_map2alm.
+ */
+sht_status sht_alm2map_ws(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream, void *scratch,
+                          size_t scratch_bytes);
+sht_status sht_map2alm_ws(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream, void *scratch,
+                          size_t scratch_bytes);
 
 /* The four stages on their own (same layouts; delta as documented above). */
 sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int nmaps, void *stream); /* eq. DeltaDef */

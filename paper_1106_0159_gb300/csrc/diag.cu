@@ -24,7 +24,40 @@ __global__ void __launch_bounds__(DIAG_T) dfma_kernel(double *out, double a, dou
     out[blockIdx.x * DIAG_T + threadIdx.x] = s;
 }
 
+// The failure path of the bounded waits: an mbarrier that expects one arrival nobody makes, polled
+// `polls` times with a short sleep like the tensor-core kernels' waits; when the poll budget runs
+// out the kernel records the timeout in the status word and returns (no trap, no hang).
+__global__ void wait_timeout_probe(int *status, long long polls)
+{
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t done = 0;
+        for (long long it = 0; it < polls && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(a), "r"(0));
+            if (!done) __nanosleep(32);
+        }
+        if (!done) atomicOr(status, 1);
+    }
+}
+
 }  // namespace
+
+// Exercise the timeout path of the device waits on the plan's status word (see the header).
+extern "C" sht_status sht_plan_selftest_timeout(sht_plan_t plan, void *stream)
+{
+    if (!plan) return SHT_EINVAL;
+    wait_timeout_probe<<<1, 32, 0, (cudaStream_t)stream>>>(plan->p.d_status, 1 << 12);
+    return cudaGetLastError() == cudaSuccess ? SHT_OK : SHT_ECUDA;
+}
 
 extern "C" sht_status sht_fp64_fma_tflops(double *tflops)
 {

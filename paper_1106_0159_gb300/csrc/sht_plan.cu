@@ -446,7 +446,7 @@ sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
     cudaError_t e = cudaMemcpy(status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && clear) e = cudaMemset(p.d_status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(p, e, "device status");
-    return SHT_OK;
+    return (*status & 1) ? SHT_ETIMEOUT : SHT_OK;
 }
 
 sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int64_t *nphi, const double *theta,
@@ -641,6 +641,46 @@ sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps,
     st = run_ring_anal(p, map, delta, scratch, nmaps, s);
     if (st != SHT_OK) return st;
     return run_legendre_anal(p, delta, (double2 *)alm, scratch, nmaps, s);
+}
+
+// The same transforms on caller-owned scratch (see the header).
+static sht_status check_ws(sht_plan_t plan, int nmaps, void *scratch, size_t scratch_bytes)
+{
+    if (!scratch || ((uintptr_t)scratch & 255u)) return SHT_EINVAL;
+    if (scratch_bytes < sht_workspace_bytes(plan, nmaps)) return SHT_EINVAL;
+    return SHT_OK;
+}
+
+sht_status sht_alm2map_ws(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream, void *scratch,
+                          size_t scratch_bytes)
+{
+    sht_status st = check_call(plan, alm, map, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    if ((st = check_ws(plan, nmaps, scratch, scratch_bytes)) != SHT_OK) return st;
+    const size_t d = align256(delta_bytes(p, nmaps));
+    double2 *delta = (double2 *)scratch;
+    double2 *sc = (double2 *)((char *)scratch + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_legendre_synth(p, (const double2 *)alm, delta, sc, nmaps, s);
+    if (st != SHT_OK) return st;
+    return run_ring_synth(p, delta, map, sc, nmaps, s);
+}
+
+sht_status sht_map2alm_ws(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream, void *scratch,
+                          size_t scratch_bytes)
+{
+    sht_status st = check_call(plan, map, alm, nmaps);
+    if (st != SHT_OK || nmaps == 0) return st;
+    Plan &p = plan->p;
+    if ((st = check_ws(plan, nmaps, scratch, scratch_bytes)) != SHT_OK) return st;
+    const size_t d = align256(delta_bytes(p, nmaps));
+    double2 *delta = (double2 *)scratch;
+    double2 *sc = (double2 *)((char *)scratch + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_ring_anal(p, map, delta, sc, nmaps, s);
+    if (st != SHT_OK) return st;
+    return run_legendre_anal(p, delta, (double2 *)alm, sc, nmaps, s);
 }
 
 sht_status sht_plan_set_stage_timing(sht_plan_t plan, int enable)

@@ -22,8 +22,9 @@ runs to the end (no kernel is interrupted) and a cancellation then only
 discards its result.  With ``batching=False`` and one stream the server is the
 plain one-at-a-time path: each request is one call, in arrival order.
 
-The transforms themselves run in the CUDA library (``sht.Plan``); this
-module only schedules.  The backend is injectable so the scheduling logic
+The transforms themselves run in the CUDA library (``sht.Plan``, one plan
+per grid and band limit shared by the stream slots, each slot with its own
+scratch); this module only schedules.  The backend is injectable so the scheduling logic
 can be exercised without a GPU (``tests/test_serve.py``).
 """
 from __future__ import annotations
@@ -245,9 +246,10 @@ def _percentile(sorted_vals, q):
 # ---------------------------------------------------------------- GPU backend
 
 class TorchBackend:
-    """Runs batches with the CUDA library: one plan per (grid, band limit, stream slot), kept on the
-    device; inputs are concatenated on the device, one transform call per batch, results split
-    back per request (device tensors)."""
+    """Runs batches with the CUDA library: one plan per (grid, band limit), kept on the device and
+    shared by the stream slots, each slot with its own scratch (sht_alm2map_ws / sht_map2alm_ws);
+    inputs are concatenated on the device, one transform call per batch, results split back per
+    request (device tensors)."""
 
     def __init__(self, mode: int = 1, device=None, nstreams: int = 2, budget_fraction: float = 0.8):
         import torch
@@ -258,7 +260,8 @@ class TorchBackend:
         self.mode = mode
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(nstreams)]
-        self.plans: Dict[Tuple[Tuple[int, int], int], Any] = {}
+        self.plans: Dict[Tuple[int, int], Any] = {}
+        self.scratch: Dict[Tuple[Tuple[int, int], int], Any] = {}
         self.resident: Dict[Tuple[Tuple[int, int], int], int] = {}
         self.budget_fraction = budget_fraction
 
@@ -266,44 +269,45 @@ class TorchBackend:
         _, total = self.torch.cuda.mem_get_info(self.device)
         return int(total * self.budget_fraction)
 
-    def plan(self, key, slot):
-        """One plan per (grid, band limit) and stream slot: a plan's scratch serves one stream."""
-        p = self.plans.get((key, slot))
+    def plan(self, key, slot=0):
+        """The plan of a (nside, lmax) key, shared by every stream slot."""
+        p = self.plans.get(key)
         if p is None:
             nside, lmax = key
             p = self.sht.Plan(self.sht.healpix_geometry(nside), lmax, lmax, grid=self.sht.GRID_HEALPIX)
             p.set_mode(self.mode)
-            self.plans[(key, slot)] = p
+            self.plans[key] = p
         return p
 
     def warm(self, keys, max_maps: int):
-        """Create every plan and reserve its scratch for `max_maps` maps, so that nothing is
-        allocated while serving, and run small transforms (1 and 17 maps, both directions) on the
-        smallest plan of each stream slot so that every kernel is loaded before the first request.
+        """Create every plan and the scratch of every (plan, stream slot) for `max_maps` maps, so
+        that nothing is allocated while serving, and run small transforms (1 and 17 maps, both
+        directions) on the smallest plan so that every kernel is loaded before the first request.
         Returns the seconds it took (plan creation is not serving)."""
         torch = self.torch
         t0 = time.perf_counter()
         for key in keys:
+            p = self.plan(key)
             for slot in range(len(self.streams)):
-                p = self.plan(key, slot)
-                p.reserve(max_maps)
+                self.scratch[(key, slot)] = p.scratch(max_maps)
                 self.resident[(key, slot)] = p.workspace_bytes(max_maps)
         small = min(keys, key=lambda k: k[1])
-        for slot in range(len(self.streams)):
-            p = self.plan(small, slot)
-            for n in (1, 17):
-                if n > max_maps:
-                    continue
-                a = torch.zeros((n, p.nalm), dtype=torch.complex128, device=self.device)
-                p.map2alm(p.alm2map(a))
+        p = self.plan(small)
+        for n in (1, 17):
+            if n > max_maps:
+                continue
+            a = torch.zeros((n, p.nalm), dtype=torch.complex128, device=self.device)
+            p.map2alm_ws(p.alm2map_ws(a, self.scratch[(small, 0)]), self.scratch[(small, 0)])
         torch.cuda.synchronize(self.device)
         return time.perf_counter() - t0
 
     def close(self):
-        """Release every plan (tables and scratch)."""
+        """Release every plan (tables) and scratch buffer."""
+        self.torch.cuda.synchronize(self.device)
         for p in self.plans.values():
             p.close()
         self.plans.clear()
+        self.scratch.clear()
         self.resident.clear()
         self.torch.cuda.empty_cache()
 
@@ -311,26 +315,30 @@ class TorchBackend:
         return sum(self.resident.values())
 
     def batch_bytes(self, key, direction, nmaps) -> int:
-        p = self.plan(key, 0)
+        p = self.plan(key)
         return nmaps * (p.nalm * 16 + p.npix * 8)
 
     def launch(self, key, direction, datas, nmaps, slot):
         torch = self.torch
-        p = self.plan(key, slot)
+        p = self.plan(key)
         st = self.streams[slot]
+        scr = self.scratch.get((key, slot))
+        if scr is None or scr.numel() < p.workspace_bytes(sum(nmaps)):
+            scr = self.scratch[(key, slot)] = p.scratch(sum(nmaps))   # a request beyond the warm-up size
+            self.resident[(key, slot)] = scr.numel()
         st.wait_stream(torch.cuda.current_stream(self.device))  # inputs were made on the caller's stream
         with torch.cuda.stream(st):
             x = datas[0] if len(datas) == 1 else torch.cat(datas, dim=0)
-            y = p.alm2map(x, stream=st) if direction == ALM2MAP else p.map2alm(x, stream=st)
+            y = p.alm2map_ws(x, scr, stream=st) if direction == ALM2MAP else p.map2alm_ws(x, scr, stream=st)
             ev = torch.cuda.Event()
             ev.record(st)
-        return (ev, y, list(nmaps), datas, x)
+        return (ev, y, list(nmaps), datas, x, scr)
 
     def done(self, handle) -> bool:
         return handle[0].query()
 
     def results(self, handle):
-        _, y, nmaps, _, _ = handle
+        y, nmaps = handle[1], handle[2]
         outs, o = [], 0
         for n in nmaps:
             outs.append(y[o:o + n])

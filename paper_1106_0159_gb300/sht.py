@@ -35,7 +35,7 @@ EXPORTS = (
     "sht_status_string", "sht_plan_last_error", "sht_plan_set_stage_timing", "sht_plan_stage_times",
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
-    "sht_plan_set_tuning", "sht_plan_tuning",
+    "sht_plan_set_tuning", "sht_plan_tuning", "sht_plan_selftest_timeout", "sht_alm2map_ws", "sht_map2alm_ws",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
@@ -96,6 +96,9 @@ def load():
             "sht_plan_reserve": (I, [P, I]),
             "sht_plan_set_tuning": (I, [P, I, I]),
             "sht_plan_tuning": (I, [P, I]),
+            "sht_plan_selftest_timeout": (I, [P, P]),
+            "sht_alm2map_ws": (I, [P, P, P, I, P, P, S]),
+            "sht_map2alm_ws": (I, [P, P, P, I, P, P, S]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -220,9 +223,16 @@ class Plan:
         return int(load().sht_plan_mode(self._h))
 
     def device_status(self, clear: bool = True) -> int:
+        """The plan's device status word (bit 0: a bounded device wait gave up); waits for the device."""
         v = ctypes.c_int()
-        _check(load().sht_plan_device_status(self._h, ctypes.byref(v), 1 if clear else 0), self._h)
+        st = load().sht_plan_device_status(self._h, ctypes.byref(v), 1 if clear else 0)
+        if st != SHT_ETIMEOUT:
+            _check(st, self._h)
         return int(v.value)
+
+    def selftest_timeout(self, stream=None):
+        """Run the failure path of the device waits once (sets bit 0 of the status word)."""
+        _check(load().sht_plan_selftest_timeout(self._h, _stream_ptr(stream)), self._h)
 
     def set_stage_timing(self, enable: bool):
         _check(load().sht_plan_set_stage_timing(self._h, 1 if enable else 0), self._h)
@@ -302,6 +312,35 @@ class Plan:
         s = self._dev(m, torch.float64, (self.npix,), "map")
         o = self._out(out, (s.shape[0], self.nalm), torch.complex128, s)
         self._run(load().sht_map2alm, s, o, s.shape[0], stream)
+        return o
+
+    def scratch(self, nmaps: int):
+        """A device scratch buffer for the *_ws calls with up to nmaps maps (uint8 tensor)."""
+        import torch
+        return torch.empty((self.workspace_bytes(nmaps),), dtype=torch.uint8, device="cuda")
+
+    def _run_ws(self, fn, src, dst, nmaps, stream, scratch):
+        if not (hasattr(scratch, "is_cuda") and scratch.is_cuda):
+            raise TypeError("scratch must be a CUDA tensor")
+        st = fn(self._h, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), int(nmaps),
+                _stream_ptr(stream), ctypes.c_void_p(scratch.data_ptr()),
+                ctypes.c_size_t(scratch.numel() * scratch.element_size()))
+        _check(st, self._h, fn.__name__)
+
+    def alm2map_ws(self, alm, scratch, out=None, stream=None):
+        """alm2map on caller scratch (from scratch()): one plan can serve several streams."""
+        import torch
+        a = self._dev(alm, torch.complex128, (self.nalm,), "alm")
+        o = self._out(out, (a.shape[0], self.npix), torch.float64, a)
+        self._run_ws(load().sht_alm2map_ws, a, o, a.shape[0], stream, scratch)
+        return o
+
+    def map2alm_ws(self, m, scratch, out=None, stream=None):
+        """map2alm on caller scratch (from scratch())."""
+        import torch
+        s = self._dev(m, torch.float64, (self.npix,), "map")
+        o = self._out(out, (s.shape[0], self.nalm), torch.complex128, s)
+        self._run_ws(load().sht_map2alm_ws, s, o, s.shape[0], stream, scratch)
         return o
 
     def legendre_synth(self, alm, out=None, stream=None):

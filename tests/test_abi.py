@@ -106,6 +106,9 @@ def test_plan_create_rejects_bad_arguments_before_device_work():
     assert lib.sht_plan_reserve(None, 1) == sht.SHT_EINVAL
     assert lib.sht_plan_set_tuning(None, 0, 4) == sht.SHT_EINVAL
     assert lib.sht_plan_tuning(None, 0) == -1
+    assert lib.sht_plan_selftest_timeout(None, None) == sht.SHT_EINVAL
+    assert lib.sht_alm2map_ws(None, None, None, 1, None, None, 0) == sht.SHT_EINVAL
+    assert lib.sht_map2alm_ws(None, None, None, 1, None, None, 0) == sht.SHT_EINVAL
     assert lib.sht_status_string(sht.SHT_EINVAL) == b"invalid argument"
     assert lib.sht_plan_last_error(None) == b""
 

@@ -74,3 +74,21 @@ def test_served_equals_alone(mode):
     st = srv.stats()
     assert st["requests"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
     print("mode", mode, "worst served-vs-alone", worst, st)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "split_bf16"])
+def test_caller_scratch_calls_match_and_check_their_scratch(mode):
+    from paper_1106_0159_gb300 import sht
+    p = sht.Plan(sht.healpix_geometry(64), 128, 128, grid=sht.GRID_HEALPIX)
+    p.set_mode(mode)
+    a = torch.from_numpy(inputs.gaussian_alm(128, 128, seed=93, nmaps=5)).cuda()
+    m = p.alm2map(a)
+    b = p.map2alm(m)
+    scr = p.scratch(5)
+    assert torch.equal(p.alm2map_ws(a, scr), m)
+    assert torch.equal(p.map2alm_ws(m, scr), b)
+    with pytest.raises(ValueError):                 # SHT_EINVAL
+        p.alm2map_ws(a, p.scratch(1)[:16])          # too small
+    with pytest.raises(ValueError):
+        p.map2alm_ws(m, scr[8:])                    # not 256-byte aligned
+    assert p.device_status() == 0
