@@ -74,14 +74,21 @@ def parse():
 
 
 MODES = {"split": "precision form: FP64 recurrence, tensor-core (tcgen05, split-bf16, 7 digits) synthesis "
-                  "and analysis sums",
+                  "sum, %s analysis sum",
          "fp64": "plain FP64"}
+
+
+def mode_desc(a, mode=None):
+    mode = mode or a.mode
+    if mode != "split":
+        return MODES[mode]
+    return MODES[mode] % ("tensor-core (split-bf16)" if a.prec_anal == "tc" else "double-float (FP32 pipe)")
 
 
 def workload_name(a, mode=None):
     return ("alm2map then map2alm round trip, HEALPix Nside=%d (%d px, %d rings), lmax=mmax=%d, "
             "%d maps per step, %s" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps,
-                                       MODES[mode or a.mode]))
+                                       mode_desc(a, mode)))
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -471,11 +478,12 @@ def ours_arm(a, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64 recurrence; bf16 digits (tcgen05, f32 accum, f64/double-float combination)" if a.mode == "split"
-                     else "f64",
+            "dtype": ("f64 recurrence; synthesis: bf16 digits (tcgen05, f32 accum, f64 combination); analysis: "
+                      + ("bf16 digits (tcgen05)" if a.prec_anal == "tc" else "double-float (f32 pairs)"))
+                     if a.mode == "split" else "f64",
             "data": DATA,
             "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": L, "mmax": L,
-                       "maps_per_step": B, "mode": MODES[a.mode],
+                       "maps_per_step": B, "mode": mode_desc(a),
                        "accuracy": "<= 1e-9 of the RMS vs the oracle" if a.mode == "split" else "<= 1e-11 of the RMS",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (a_lm %.2f GB, maps %.2f GB per step)"
