@@ -68,8 +68,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
-    ap.add_argument("--prec-anal", default="df", choices=["df", "tc"],
-                    help="precision-form analysis kernel: double-float (default) or tensor cores")
+    ap.add_argument("--prec-anal", default="tc", choices=["df", "tc"],
+                    help="precision-form analysis kernel: tensor cores (default) or double-float")
     return ap.parse_args()
 
 
@@ -330,10 +330,12 @@ def ours_arm(a, rank, world, local_rank):
                     "peak_source": "derived: 128 FP32 FMA/clk/SM x %d SMs x %d MHz x 2 flop" % (nsm, SM_MAX_MHZ),
                     "work": "30 FP32 flops per (l, m, ring-pair, map): two double-float real products and sums"}
         # tensor-core kernels: bound by their FP64 recurrence (2 DFMA per (l, m, ring-pair) step,
-        # once per launch: 8 maps per analysis launch, 16 per synthesis launch); the contraction's
-        # useful tensor work is 28 digit products x 2 flops per step and real column (2 per map)
+        # once per launch of up to 16 maps); the contraction's useful tensor work is 28 digit
+        # products x 2 flops per step and real column (2 per map).  The stage time includes the
+        # polar-block FP64 kernels (and the block reduction of the analysis), so this is a lower
+        # bound on the kernel's own rate
         ms = st["legendre_anal"][0] if anal else st["legendre_synth"][0]
-        per = 8 if anal else 16
+        per = 16
         launches = -(-B // per)
         achieved = 4.0 * S * launches * steps / (ms * 1e-3) / 1e12
         tensor = 56.0 * S * 2 * B * steps / (ms * 1e-3) / 1e12

@@ -78,13 +78,16 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings,
                            const double *w, int lmax, int mmax);
 
 /*
- * Arithmetic of the Legendre synthesis (the analysis is FP64 in both modes):
+ * Arithmetic of the transforms:
  *   SHT_MODE_FP64        (default) every step in FP64.
- *   SHT_MODE_SPLIT_BF16  the lambda recurrence in FP64, the sum over l of eq. (matrix_vec) on the
- *                        tensor cores: both operands cut into six balanced 7-bit digits, digit
- *                        products accumulated exactly in FP32, combined in FP64.  Relative error
- *                        against the exact transform <= 1e-9 of the output RMS.  Processes up to
- *                        16 maps per pass over the recurrence.
+ *   SHT_MODE_SPLIT_BF16  the precision form.  The lambda recurrence stays in FP64.  The sums of
+ *                        eq. (matrix_vec) run on the tensor cores: the sum over l of the synthesis
+ *                        and the sum over rings of the analysis, both operands cut into seven
+ *                        balanced 7-bit digits, digit products accumulated in FP32 and combined in
+ *                        FP64 or double-float.  The ring DFTs run in double-float on the FP32 pipe.
+ *                        SHT_TUNE_PREC_ANAL and SHT_TUNE_PREC_RING select other kernels.  Relative
+ *                        error against the exact transform <= 1e-9 of the output RMS.  Processes up
+ *                        to 16 maps per pass over the recurrence.
  * Switching to SHT_MODE_SPLIT_BF16 the first time runs one FP64 pass of the recurrence to
  * measure the scale of its values per (m, block of 128 ring slots) (synchronous; about the cost
  * of one single-map synthesis).  SHT_EINVAL for an unknown mode.
@@ -184,7 +187,7 @@ typedef enum {
     SHT_TUNE_ANAL_SLOTS = 2, /* FP64 analysis: ring slots per thread, 1 or 4 (default 4, or 1 below 512 slots) */
     SHT_TUNE_DF_MAPS = 3,    /* precision-form analysis: maps per launch, 4, 8 or 16 (default 8) */
     SHT_TUNE_TC_MAPS = 4,    /* precision-form synthesis: maps per tensor-core launch, 8 or 16 (default 16) */
-    SHT_TUNE_PREC_ANAL = 5,  /* precision-form analysis kernel: 0 double-float FP32 (default), 1 tensor cores */
+    SHT_TUNE_PREC_ANAL = 5,  /* precision-form analysis kernel: 0 double-float FP32, 1 tensor cores (default) */
     SHT_TUNE_PREC_RING = 6,  /* precision-form ring DFTs: 1 double-float FP32 (default), 0 FP64 */
     SHT_TUNE_COUNT = 7
 } sht_tune;

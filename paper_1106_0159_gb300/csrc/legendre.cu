@@ -600,9 +600,10 @@ cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, doubl
 }
 
 // The Reinsch-form analysis CTAs only (slot block 0 of `slots` slots, m <= mR), writing FP64
-// partials into block 0 of the caller's partial buffer ([nblk][nmaps][nalm], 16 B per entry).
+// partials of a_lm index i < index(mR + 1, mR + 1) for map g to partial[g * map_stride + i]
+// (block 0 of a [nblk][nmaps][nalm] buffer: map_stride = nalm).
 cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, double2 *partial, int nmaps, int slots,
-                                       cudaStream_t st, int *nlaunch)
+                                       int64_t map_stride, cudaStream_t st, int *nlaunch)
 {
     *nlaunch = 0;
     if (p.mR < 0 || !p.polar_first_slot) return cudaSuccess;
@@ -622,13 +623,13 @@ cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, doub
     A.mmax = p.mmax;
     A.nrings = p.nrings;
     A.nalm = p.nalm;
-    A.part_map_stride = p.nalm;
-    A.part_blk_stride = (int64_t)nmaps * p.nalm;
+    A.part_map_stride = map_stride;
+    A.part_blk_stride = 0;  // block 0 only
     const unsigned grid = (unsigned)(p.mR + 1);
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     for (int g0 = 0; g0 < nmaps;) {
         A.delta = delta + (int64_t)g0 * dstride;
-        A.partial = partial + (int64_t)g0 * p.nalm;
+        A.partial = partial + (int64_t)g0 * map_stride;
         if (nmaps - g0 >= 4) {  // the Reinsch recurrence (4 DFMA per step) runs once per launch
             if (slots == ANA_T)
                 legendre_anal_kernel<4, 1><<<grid, ANA_T, 0, st>>>(A);

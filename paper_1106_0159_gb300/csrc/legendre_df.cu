@@ -295,29 +295,38 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 // a_lm = c_lm * sum over blocks of (hi + lo).  The blocks are added in order as double-float
 // pairs on the FP32 pipe (widening each partial to FP64 and adding there made this kernel
 // FP64-bound: four conversions and four adds per complex value and block) and the sum is widened
-// once.  Block 0 holds FP64 partials (double2, from the Reinsch kernel) for the indices below
-// fp64_lim, i.e. for m <= mR of a polar plan; they enter the sum split into hi + lo.
+// once.  Partial (block, map g, index i) sits at bk * blk_stride + g * map_stride + i * idx_stride:
+// [block][map][index] from the double-float kernel, [block][index][map] from the tensor-core one;
+// threads walk the innermost of the two.  For i < fp64_lim (m <= mR of a polar plan) the block-0
+// term is the Reinsch kernel's FP64 partial polar[g * polar_stride + i], split into hi + lo.
 __device__ __forceinline__ double widen_df(float2 a) { return (double)a.x + (double)a.y; }
 
-__global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double *__restrict__ cfac,
+__global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double2 *__restrict__ polar,
+                                        int64_t polar_stride, const double *__restrict__ cfac,
                                         double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
-                                        int64_t blk_stride, int64_t fp64_lim)
+                                        int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim)
 {
     const int64_t total = nalm * nmaps;
+    const bool maps_inner = map_stride < idx_stride;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = t / nalm, i = t - g * nalm;
-        const float4 *src = partial + g * nalm + i;
+        int64_t g, i;
+        if (maps_inner) {
+            i = t / nmaps;
+            g = t - i * nmaps;
+        } else {
+            g = t / nalm;
+            i = t - g * nalm;
+        }
+        const float4 *src = partial + g * map_stride + i * idx_stride;
         float2 re, im;
-        {
+        if (i < fp64_lim) {
+            const double2 d = polar[g * polar_stride + i];
+            re = d2df(d.x);
+            im = d2df(d.y);
+        } else {
             const float4 v = src[0];
-            if (i < fp64_lim) {
-                const double2 d = *reinterpret_cast<const double2 *>(&v);
-                re = d2df(d.x);
-                im = d2df(d.y);
-            } else {
-                re = make_float2(v.x, v.y);
-                im = make_float2(v.z, v.w);
-            }
+            re = make_float2(v.x, v.y);
+            im = make_float2(v.z, v.w);
         }
 #pragma unroll 4
         for (int bk = 1; bk < nblk; ++bk) {
@@ -326,7 +335,7 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
             im = df_add(im, make_float2(v.z, v.w));
         }
         const double c = cfac[i];
-        alm[t] = make_double2(c * widen_df(re), i <= lmax ? 0.0 : c * widen_df(im));
+        alm[g * nalm + i] = make_double2(c * widen_df(re), i <= lmax ? 0.0 : c * widen_df(im));
     }
 }
 
@@ -349,12 +358,15 @@ cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
 
 }  // namespace
 
-cudaError_t launch_reduce_blocks_df(const float4 *partial, const double *cfac, double2 *alm, int nblk, int64_t nalm,
-                                    int nmaps, int lmax, int64_t blk_stride, int64_t fp64_lim, cudaStream_t st)
+cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
+                                    const double *cfac, double2 *alm, int nblk, int64_t nalm, int nmaps, int lmax,
+                                    int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim,
+                                    cudaStream_t st)
 {
     const int64_t total = nalm * nmaps;
     const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, cfac, alm, nblk, nalm, nmaps, lmax, blk_stride, fp64_lim);
+    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, polar, polar_stride, cfac, alm, nblk, nalm, nmaps, lmax,
+                                                   blk_stride, map_stride, idx_stride, fp64_lim);
     return cudaGetLastError();
 }
 
@@ -409,19 +421,17 @@ cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2
         g0 += nm;
     }
     int64_t fp64_lim = 0;
-    if (A.mR >= 0) {
+    if (A.mR >= 0) {  // FP64 partials in place of block 0 for m <= mR
         int n = 0;
-        cudaError_t e = launch_legendre_anal_polar(p, delta, (double2 *)partial, nmaps, DF_T, st, &n);
+        cudaError_t e = launch_legendre_anal_polar(p, delta, (double2 *)partial, nmaps, DF_T, p.nalm, st, &n);
         *nlaunch += n;
         if (e != cudaSuccess) return e;
         fp64_lim = (int64_t)(A.mR + 1) * (2 * (int64_t)p.lmax + 3 - (A.mR + 1)) / 2;  // index(mR+1, mR+1)
     }
-    const int64_t total = p.nalm * nmaps;
-    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>((const float4 *)partial, p.d_cfac, alm, A.nblk, p.nalm, nmaps,
-                                                   p.lmax, A.part_blk_stride, fp64_lim);
+    cudaError_t e = launch_reduce_blocks_df((const float4 *)partial, (const double2 *)partial, p.nalm, p.d_cfac, alm,
+                                            A.nblk, p.nalm, nmaps, p.lmax, A.part_blk_stride, p.nalm, 1, fp64_lim, st);
     ++*nlaunch;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace sht

@@ -235,7 +235,7 @@ struct TcTile {
 
 struct TcArgs {
     const double2 *alm;      // [nmaps][nalm], first map of this group
-    double2 *delta;          // [nmaps][nrings][mmax+1]
+    double2 *delta;          // [nmaps][nrings][mmax+1] (synthesis: written; analysis: read)
     const int *slotN, *slotS;
     const double *u, *s;
     const double *alpha, *cfac;
@@ -247,6 +247,7 @@ struct TcArgs {
     const int64_t *chunk_base;  // [mmax+1] first chunk of each m
     const int *chunk_m;      // [total chunks] m of each chunk
     uint4 *bdig;             // [total chunks][B_CHUNK / 16]
+    float4 *partial;         // analysis: [nblk][nalm][nmaps] (re_hi, re_lo, im_hi, im_lo) of a_lm / c_lm per block
     int *status;             // device status word (bit 0: an mbarrier wait timed out)
     int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
     int64_t nalm;
@@ -473,10 +474,69 @@ struct TcWs {
 
 constexpr int TC_NT = 3 * TC_T;  // threads per synthesis CTA: 4 recurrence warps + 8 split warps
 
+// The recurrence warps (threads 0-127, thread r = slot r of the block) of the tensor-core kernels:
+// from the plan-time checkpoint at chunk cfirst & ~1 (earlier chunks hold only dropped values)
+// they run the two-instruction y recurrence and write each live chunk's 32 values (0 where
+// dropped) to y stage q & 1, laid out [32 l][YS doubles].  alpha comes from a register of lane j
+// (warp shuffle), loaded one chunk ahead.  Stages are handed over with named barriers over all
+// TC_NT threads: FULL (arrive here, the split warps wait) and EMPTY (the split warps arrive,
+// wait here, only where a later chunk reuses the stage).
+template <int YS>
+__device__ __forceinline__ void recurrence_warps(const TcArgs &A, int m, int blk, int r, bool active, int64_t base,
+                                                 int nch, int cfirst, double *ybuf)
+{
+    const int lane = r & 31;
+    const int L = A.lmax;
+    const int c0 = cfirst & ~1;
+    double u = 0.0, y1 = 0.0, y2 = 0.0;
+    int k = 0;
+    if (active) {
+        u = A.u[blk * TC_T + r];
+        const int64_t ci = (int64_t)(m * A.nblk + blk) * TC_T + r;
+        const double2 st = A.ck_y[ci];
+        y1 = st.x;
+        y2 = st.y;
+        k = A.ck_k[ci];
+    }
+    double al_next = (m + TC_CH * c0 + lane <= L) ? A.alpha[base + TC_CH * c0 + lane] : 0.0;
+    for (int c = c0; c < nch; ++c) {
+        const int l0 = m + TC_CH * c;
+        const double al_cur = al_next;
+        {
+            const int ln = l0 + TC_CH + lane;
+            al_next = (c + 1 < nch && ln <= L) ? A.alpha[base + (ln - m)] : 0.0;
+        }
+        const int q = c - cfirst;  // live chunk index
+        double *yb = ybuf + (size_t)(q & 1) * TC_CH * YS;
+        if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), TC_NT);  // the split warps read chunk q - 2
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const bool scaled = __any_sync(0xffffffffu, k < 0);
+            const bool drop = scaled && k < 0;
+#pragma unroll
+            for (int j = 16 * h; j < 16 * h + 16; ++j) {
+                // alpha x = alpha (1 - u) does not depend on y, so each step adds one DFMA
+                // (not two) to the dependency chain: one chain per SMSP is latency-bound
+                const double a = __shfl_sync(0xffffffffu, al_cur, j);
+                const double ax = fma(-a, u, a);
+                const double y = fma(ax, y1, -y2);
+                y2 = y1;
+                y1 = y;
+                if (q >= 0) yb[j * YS + r] = drop ? 0.0 : y;
+            }
+            if (drop && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                y1 *= 0x1p-512;
+                y2 *= 0x1p-512;
+                k += 1;
+            }
+        }
+        if (q >= 0) bar_arrive(BAR_FULL + (q & 1), TC_NT);
+    }
+}
+
 // Warp groups per CTA (one m, 128 slots, 384 threads):
-//   recurrence warps 0-3: thread r runs the FP64 recurrence of slot r and writes each chunk's 32
-//     values (0 where dropped) to a double-buffered y stage in shared memory; alpha comes from a
-//     register of lane j (warp shuffle), loaded one chunk ahead;
+//   recurrence warps 0-3 (recurrence_warps): thread r runs the FP64 recurrence of slot r and
+//     writes each chunk's 32 values to a double-buffered y stage in shared memory;
 //   split warps 4-11: thread (par, r) cuts the 16 values of parity par of slot r into digits and
 //     stores row r of the parity's A tiles (double-buffered); all of them copy the chunk's a_lm
 //     digit tiles; lane 0 of warps 4-7 issues the MMAs of one (parity, class group) each and
@@ -544,54 +604,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 
     bool ok = true;
     if (rec) {
-        // ------------------------------------------------ recurrence group
-        // from the plan-time checkpoint at chunk c0 = cfirst & ~1 (earlier chunks are all dropped)
-        const int c0 = cfirst & ~1;
-        double u = 0.0, y1 = 0.0, y2 = 0.0;
-        int k = 0;
-        if (active) {
-            u = A.u[slot];
-            const int64_t ci = (int64_t)(m * A.nblk + blk) * TC_T + r;
-            const double2 st = A.ck_y[ci];
-            y1 = st.x;
-            y2 = st.y;
-            k = A.ck_k[ci];
-        }
-        // lane j holds alpha of step j of the current chunk and loads the next chunk's ahead
-        double al_next = (m + TC_CH * c0 + lane <= L) ? A.alpha[base + TC_CH * c0 + lane] : 0.0;
-        for (int c = c0; c < nch; ++c) {
-            const int l0 = m + TC_CH * c;
-            const double al_cur = al_next;
-            {
-                const int ln = l0 + TC_CH + lane;
-                al_next = (c + 1 < nch && ln <= L) ? A.alpha[base + (ln - m)] : 0.0;
-            }
-            const int q = c - cfirst;  // live chunk index
-            double *yb = ybuf + (size_t)(q & 1) * TC_CH * TC_T;
-            if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), TC_NT);  // the split group read chunk q - 2
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const bool scaled = __any_sync(0xffffffffu, k < 0);
-                const bool drop = scaled && k < 0;
-#pragma unroll
-                for (int j = 16 * h; j < 16 * h + 16; ++j) {
-                    // alpha x = alpha (1 - u) does not depend on y, so each step adds one DFMA
-                    // (not two) to the dependency chain: one chain per SMSP is latency-bound
-                    const double a = __shfl_sync(0xffffffffu, al_cur, j);
-                    const double ax = fma(-a, u, a);
-                    const double y = fma(ax, y1, -y2);
-                    y2 = y1;
-                    y1 = y;
-                    if (q >= 0) yb[j * TC_T + r] = drop ? 0.0 : y;
-                }
-                if (drop && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
-                    y1 *= 0x1p-512;
-                    y2 *= 0x1p-512;
-                    k += 1;
-                }
-            }
-            if (q >= 0) bar_arrive(BAR_FULL + (q & 1), TC_NT);
-        }
+        recurrence_warps<TC_T>(A, m, blk, r, active, base, nch, cfirst, ybuf);
     } else {
         // ------------------------------------------------ split / MMA group
         const uint32_t idesc = umma_idesc<N>();
@@ -726,61 +739,51 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 
 // ---------------------------------------------------------------- the analysis kernel
 //
-// a_lm = c_lm sum over ring slots of y_lm(slot) X(slot), X = Sigma = Delta_N + Delta_S for even
-// l - m and D = Delta_N - Delta_S for odd (eq. almdef, Algorithm 5), as the matrix product
-// [l x slots] . [slots x columns] per m and slot block, on the tensor cores: M = 64 values of l,
-// K = 16 slots per MMA, N = [Sigma | D] columns (2 per map each; a row uses the half of its
-// parity).  Both operands are cut into 7 digits as in the synthesis: y with the per-(m, block)
-// exponent of tc_ymax_kernel, X with a per-(m, block, column) exponent measured in the CTA.
-// Digit products i + j <= 6 go into five FP32 accumulators (classes 0-3 and 4-6), which over
-// the 128 slots of a block stay far inside 24 bits.  Per chunk of 64 l the epilogue adds the
-// classes as double-float pairs (FP32 pipe) and writes the block's partial a_lm / c_lm, which
-// the block reduction sums in FP64 and multiplies by c_lm.
+// a_lm = c_lm sum over ring slots of y_lm(slot) X_m(slot), X = Sigma = Delta_N + Delta_S for even
+// l - m and X = D = Delta_N - Delta_S for odd (eq. almdef, Algorithm 5).  For one m and a block
+// of 128 slots this is the product [columns x slots] . [slots x l] (eq. matrix_vec transposed),
+// run on the tensor cores with the map columns as the MMA rows: M = 64 rows (Sigma and D, re and
+// im, of up to 16 maps), K = 16 slots per MMA, N = 32 values of l (one 32-l chunk, its 16
+// even-parity values first).  Each row keeps the columns of its parity; the other half is
+// computed and dropped, which is cheap with the tensor pipe mostly idle.  The X digits of the
+// whole block (the A operand, 7 x 16 KB) are cut once per CTA and the y digits (B operand) per
+// K-step, so one launch serves 16 maps with one pass of the FP64 recurrence, which bounds it.
 //
-// CTA: one m, 128 slots, 256 threads: four recurrence warps write a double-buffered y stage of
-// 64 l per chunk (the same recurrence as the synthesis); four split warps build, per K-step of
-// 16 slots, the A tiles (one row of 8 slots of one l per thread, double-buffered), two of them
-// issue the 28 MMAs of the step (classes 0-3 / merged class 4-6), and at the end of a chunk all
-// four read the accumulators: with M = 64 the rows sit in lanes 0-15 of each 32-lane quarter
-// of tensor memory (measured), so each warp takes 16 rows.
+// Digits as in the synthesis: 7 balanced base-128 digits, products i + j <= 6 into five FP32
+// accumulators, y with the per-(m, block) exponent of tc_ymax_kernel and X with a per-(m, block,
+// row) exponent measured in the CTA.  Over 128 slots the class sums stay below 2^19 (exact in
+// FP32 for classes 0-3).  A chunk's accumulators (5 x 32 columns) are double-buffered in tensor
+// memory: the epilogue of chunk q - 1 runs while the MMAs of chunk q are issued.  It adds the
+// classes as double-float pairs (FP32 pipe) and writes the block's partial a_lm / c_lm,
+// [block][index][map], which the block reduction sums and multiplies by c_lm.
+//
+// CTA: one m, 128 slots, 384 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
+// 32 l); split warps 4-11 cut the y values of each K-step into the double-buffered B tiles, lane 0
+// of warps 4 and 5 issues the K-step's 28 MMAs (classes 0-3 / the merged class 4-6) and commits
+// them to the buffer's mbarrier, and all eight read the previous chunk's accumulators: with
+// M = 64, row r sits in lane 32 (r / 16) + r % 16 of tensor memory, so warps w and w + 4 share
+// one lane quarter and take 8 of its columns each.
 
-constexpr int TA_CH = 64;            // l per analysis chunk = MMA M
-constexpr int TA_NT = 2 * TC_T;      // 4 recurrence + 4 split warps
-constexpr int TA_YS = TC_T + 1;      // y stage row stride in doubles (odd: conflict-free split reads)
-constexpr int TA_MAPS = 8;           // maps per launch (N = 4 maps = 32 columns)
+constexpr int TA_M = 64;                          // MMA rows: [Sigma | D] x 16 maps x (re, im)
+constexpr int TA_MAPS = 16;                       // maps per launch
+constexpr int TA_YS = TC_T + 4;                   // y stage row stride (doubles): conflict-free pair loads
+constexpr int TA_ADIG = TA_M * TC_T * 2;          // one digit of the X operand [64 x 128 slots] bf16
+constexpr int TA_BDIG = TC_CH * 16 * 2;           // one digit of a K-step's y tile [32 l x 16 slots] bf16
+constexpr int TA_ACC = TC_NACC * TC_CH;           // tensor-memory columns of one chunk's accumulators
+constexpr int TA_OFF_B = TC_S * TA_ADIG;
+constexpr int TA_OFF_Y = TA_OFF_B + 2 * TC_S * TA_BDIG;
+constexpr int TA_OFF_E = TA_OFF_Y + 2 * TC_CH * TA_YS * 8;
+constexpr int TA_OFF_BAR = TA_OFF_E + TA_M * 4;
+constexpr int TA_SMEM = TA_OFF_BAR + 64 + 1024;   // + alignment slack
+constexpr int TA_TMEM_COLS = 512;                 // two chunks of accumulators
+static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
+static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
 
 template <int M, int N>
 __device__ __forceinline__ uint32_t umma_idesc_mn()
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-
-struct TaArgs {
-    const double2 *delta;    // [nmaps][nrings][mmax+1], first map of this group
-    float4 *partial;         // [nblk][nmaps][nalm]: (re_hi, re_lo, im_hi, im_lo) of a_lm / c_lm per block
-    const int *slotN, *slotS;
-    const double *u, *s, *alpha;
-    const int *Ey, *first;   // per (m, slot block of 128): y exponent, first live 32-l chunk
-    const double2 *ck_y;     // recurrence state at 32-l chunk first & ~1, per slot
-    const int *ck_k;
-    int *status;
-    int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
-    int64_t nalm;
-};
-
-template <int N>  // N = 4 x maps: Sigma (re, im) for each map, then D (re, im)
-struct TaWs {
-    static constexpr int B_DIG = TC_T * N * 2;             // one digit of [N x 128 slots] bf16
-    static constexpr int A_KS = TA_CH * 16 * 2;            // one digit of a K-step tile [64 l x 16 slots]
-    static constexpr int Y_BYTES = TA_CH * TA_YS * 8;      // one y stage
-    static constexpr int OFF_A = TC_S * B_DIG;
-    static constexpr int OFF_Y = OFF_A + 2 * TC_S * A_KS;
-    static constexpr int OFF_E = OFF_Y + 2 * Y_BYTES;
-    static constexpr int OFF_BAR = OFF_E + 4 * N;
-    static constexpr int SMEM = OFF_BAR + 64 + 1024;
-    static constexpr int NACC = TC_NACC;
-    static constexpr int TMEM_COLS = (NACC * N <= 128) ? 128 : 256;
-};
 
 __device__ __forceinline__ float2 two_sum(float a, float b)
 {
@@ -789,17 +792,14 @@ __device__ __forceinline__ float2 two_sum(float a, float b)
     return make_float2(s, (a - (s - bb)) + (b - bb));
 }
 
-template <int N>
-__global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TaArgs A)
+__global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    using W = TaWs<N>;
-    constexpr int G = N / 4;  // maps of this launch (at most)
-    unsigned char *sB = smem;                               // [digit][N x 128] bf16, K-major
-    unsigned char *sA = smem + W::OFF_A;                    // [buffer][digit][64 x 16] bf16
-    double *ybuf = (double *)(smem + W::OFF_Y);             // [stage][64 l][TA_YS]
-    int *sEx = (int *)(smem + W::OFF_E);                    // [N] column exponents
-    uint64_t *mbar = (uint64_t *)(smem + W::OFF_BAR);       // [A buffer]
+    unsigned char *sX = smem;                               // [digit][64 x 128] bf16, K-major (A operand)
+    unsigned char *sY = smem + TA_OFF_B;                    // [buffer][digit][32 x 16] bf16, K-major (B operand)
+    double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
+    int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
+    uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // [B buffer]
     uint32_t *tslot = (uint32_t *)(mbar + 2);
 
     const int m = blockIdx.x / A.nblk;
@@ -808,41 +808,38 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TaArgs A)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool rec = warp < 4;
-    const int sp = tid - TC_T;                              // split-thread index 0..127
-    const int r = rec ? tid : sp;
+    const int sp = tid - TC_T;                              // split-thread index 0..255
+    const int r = rec ? tid : (sp & (TC_T - 1));            // slot within the block
     const int slot = blk * TC_T + r;
     const bool active = slot < A.nslots;
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
-    const int nch = (L - m + TA_CH) / TA_CH;
-    const int cfirst = A.first[m * A.nblk + blk] / 2;      // first 64-l chunk with a kept value
+    const int nch = (L - m + TC_CH) / TC_CH;
+    const int cfirst = A.first[m * A.nblk + blk];           // chunks before it hold only dropped values
     const int nlive = nch - cfirst;
-    const int64_t pstride = (int64_t)A.nmaps * A.nalm;
-    float4 *part = A.partial + (int64_t)blk * pstride;
+    const int nm = A.nmaps;
+    float4 *part = A.partial + (int64_t)blk * A.nalm * nm;  // this block's [index][map]
 
-    // rows of l before the first live chunk hold only dropped values: zero partials
+    // l before the first live chunk: zero partials
     {
-        const int dead = min(TA_CH * cfirst, L - m + 1);
-        const int t0 = rec ? tid + TC_T : sp;  // all 256 threads
-        for (int t = t0; t < dead * A.nmaps; t += TA_NT) {
-            const int g = t / dead, j = t - g * dead;
-            part[(int64_t)g * A.nalm + base + j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        const int64_t dead = (int64_t)min(TC_CH * cfirst, L - m + 1) * nm;
+        float4 *p0 = part + base * nm;
+        for (int64_t t = tid; t < dead; t += TC_NT) p0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (nlive <= 0) return;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(W::TMEM_COLS));
+                     "r"(TA_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        // two issuing threads (class groups) commit to each A buffer's mbarrier
+        // two issuing threads (class groups) commit to each B buffer's mbarrier
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(2));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(2));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (tid < N) sEx[tid] = 0;
+    if (tid < TA_M) sEx[tid] = 0;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -850,211 +847,171 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TaArgs A)
 
     bool ok = true;
     if (rec) {
-        // ------------------------------------------------ recurrence group (as in the synthesis)
-        // from the plan-time checkpoint at 64-l chunk cfirst (32-l chunk 2 cfirst)
-        double u = 0.0, y1 = 0.0, y2 = 0.0;
-        int k = 0;
-        if (active) {
-            u = A.u[slot];
-            const int64_t ci = (int64_t)(m * A.nblk + blk) * TC_T + r;
-            const double2 st = A.ck_y[ci];
-            y1 = st.x;
-            y2 = st.y;
-            k = A.ck_k[ci];
-        }
-        const int la = TA_CH * cfirst;
-        double an0 = (m + la + lane <= L) ? A.alpha[base + la + lane] : 0.0;
-        double an1 = (m + la + 32 + lane <= L) ? A.alpha[base + la + 32 + lane] : 0.0;
-        for (int c = cfirst; c < nch; ++c) {
-            const int l0 = m + TA_CH * c;
-            const double a0c = an0, a1c = an1;
-            {
-                const int ln = l0 + TA_CH + lane;
-                an0 = (c + 1 < nch && ln <= L) ? A.alpha[base + (ln - m)] : 0.0;
-                an1 = (c + 1 < nch && ln + 32 <= L) ? A.alpha[base + (ln + 32 - m)] : 0.0;
-            }
-            const int q = c - cfirst;
-            double *yb = ybuf + (size_t)(q & 1) * TA_CH * TA_YS;
-            if (q >= 2) bar_sync(BAR_EMPTY + (q & 1), TA_NT);
-#pragma unroll 1
-            for (int h = 0; h < 4; ++h) {  // quarters of 16 steps: the rescaling cadence of the synthesis
-                const bool scaled = __any_sync(0xffffffffu, k < 0);
-                const bool drop = scaled && k < 0;
-                const double acur = (h < 2) ? a0c : a1c;
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = 16 * h + jj;
-                    const double a = __shfl_sync(0xffffffffu, acur, (16 * h + jj) & 31);
-                    const double ax = fma(-a, u, a);
-                    const double y = fma(ax, y1, -y2);
-                    y2 = y1;
-                    y1 = y;
-                    if (q >= 0) yb[j * TA_YS + r] = (drop || !active) ? 0.0 : y;
-                }
-                if (drop && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
-                    y1 *= 0x1p-512;
-                    y2 *= 0x1p-512;
-                    k += 1;
-                }
-            }
-            if (q >= 0) bar_arrive(BAR_FULL + (q & 1), TA_NT);
-        }
+        recurrence_warps<TA_YS>(A, m, blk, r, active, base, nch, cfirst, ybuf);
     } else {
-        // ------------------------------------------------ split / MMA / epilogue group
+        // ------------------------------------------------ X digits, then split / MMA / epilogue
         const int Ey = A.Ey[m * A.nblk + blk];
-        // Sigma | D of this slot for the maps of this launch, their column exponents and digits
-        double xv[N];
+        const int hh = sp >> 7;  // this thread's maps: 8 hh .. 8 hh + 7 of slot r
+        double xv[2][8][2];      // [Sigma, D][map][re, im] -> row 32 s + 2 g + c
         {
             const int rn = active ? A.slotN[slot] : -1, rs = active ? A.slotS[slot] : -1;
             const int64_t mstride = A.mmax + 1;
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
+            for (int gg = 0; gg < 8; ++gg) {
+                const int g = 8 * hh + gg;
                 double2 dn = make_double2(0.0, 0.0), ds = make_double2(0.0, 0.0);
-                if (g < A.nmaps) {
+                if (g < nm) {
                     const double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
                     if (rn >= 0) dn = d[(int64_t)rn * mstride + m];
                     if (rs >= 0) ds = d[(int64_t)rs * mstride + m];
                 }
-                xv[2 * g] = dn.x + ds.x;
-                xv[2 * g + 1] = dn.y + ds.y;
-                xv[N / 2 + 2 * g] = dn.x - ds.x;
-                xv[N / 2 + 2 * g + 1] = dn.y - ds.y;
-            }
-#pragma unroll
-            for (int n = 0; n < N; ++n) {
-                const int e = dexp(xv[n]);
-                if (e) atomicMax(&sEx[n], e);
+                xv[0][gg][0] = dn.x + ds.x;
+                xv[0][gg][1] = dn.y + ds.y;
+                xv[1][gg][0] = dn.x - ds.x;
+                xv[1][gg][1] = dn.y - ds.y;
             }
         }
-        bar_sync(BAR_SPLIT, TC_T);
-#pragma unroll 1
-        for (int n = 0; n < N; ++n) {
-            const int e = sEx[n];
-            float d[TC_S];
-            split_digits(xv[n], e ? e - 1022 : -1000, d);
-            // B operand, K-major [N x 128]: element (n, k = r)
-            const int off = ((r >> 3) * (N / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (r & 7) * 2;
 #pragma unroll
-            for (int s = 0; s < TC_S; ++s) *(__nv_bfloat16 *)(sB + s * W::B_DIG + off) = __float2bfloat16_rn(d[s]);
-        }
-        const uint32_t idesc = umma_idesc_mn<TA_CH, N>();
-        const int row = sp & (TA_CH - 1), kh = sp >> 6;   // this thread's A-tile row and 8-slot half
-        const int lw = warp & 3;                             // tensor-memory lane quarter of this warp
-        int gk = 0;                                          // K-steps issued so far (all chunks)
-        for (int q = 0; q < nlive; ++q) {
-            const int c = cfirst + q;
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int e = dexp(xv[s][gg][c]);
+                    if (e) atomicMax(&sEx[32 * s + 2 * (8 * hh + gg) + c], e);
+                }
+        bar_sync(BAR_SPLIT, 2 * TC_T);
+        // A operand, K-major [64 x 128]: element (row, k = r) in core matrix (row / 8, r / 8)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int row = 32 * s + 2 * (8 * hh + gg) + c;
+                    const int e = sEx[row];
+                    float d[TC_S];
+                    split_digits(xv[s][gg][c], e ? e - 1022 : -1000, d);
+                    const int off = ((r >> 3) * (TA_M / 8) + (row >> 3)) * 128 + (row & 7) * 16 + (r & 7) * 2;
+#pragma unroll
+                    for (int q = 0; q < TC_S; ++q)
+                        *(__nv_bfloat16 *)(sX + q * TA_ADIG + off) = __float2bfloat16_rn(d[q]);
+                }
+
+        const uint32_t idesc = umma_idesc_mn<TA_M, TC_CH>();
+        const int w8 = warp - 4;  // 0..7
+        // B tile element pair of this thread per K-step: row n (l - l0 = 2 (n % 16) + n / 16),
+        // slots 2 kp, 2 kp + 1 of 8-slot half kh
+        const int kp = lane & 3, nlo = lane >> 2, nhi = w8 & 3, kh = w8 >> 2;
+        const int n = 8 * nhi + nlo;
+        const int jrow = 2 * (n & 15) + (n >> 4);
+        const int boff = (kh * (TC_CH / 8) + nhi) * 128 + nlo * 16 + kp * 4;
+        // epilogue: lane quarter qd; rows 16 qd .. 16 qd + 15 are Sigma (qd < 2, even l - m) or D
+        // rows (odd), of maps 8 (qd & 1) + lane / 2, re or im by lane parity; columns n0 .. n0 + 7
+        const int qd = warp & 3, hf = w8 >> 2;
+        const int erow = 16 * qd + (lane & 15);
+        const int es = qd >> 1;
+        const int eg = 8 * (qd & 1) + ((lane & 15) >> 1), ec = lane & 1;
+        const int n0 = 16 * es + 8 * hf;
+        int gk = 0;  // K-steps so far (all chunks)
+        for (int q = 0; q <= nlive; ++q) {
             const int st = q & 1;
-            bar_sync(BAR_FULL + st, TA_NT);  // y of chunk q is in its stage
-            const double *yb = ybuf + (size_t)st * TA_CH * TA_YS;
+            if (q < nlive) bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
+            if (q >= 1) {
+                // ---- epilogue of chunk q - 1: its last commit covers all its MMAs
+                const int qe = q - 1, tb = qe & 1, gl = gk - 1;
+                if (ok && !mbar_wait(&mbar[gl & 1], (uint32_t)((gl >> 1) & 1))) ok = false;
+                ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (ok) {
+                    float2 acc[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int cls = 0; cls < TC_NACC; ++cls) {
+                        uint32_t v[8];
+                        const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(tb * TA_ACC + cls * TC_CH + n0);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                       "=r"(v[6]), "=r"(v[7])
+                                     : "r"(addr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+                        // the digits carry their weights 2^(-7 s), so the classes add as they are, in
+                        // decreasing size: a double-float sum keeps them all
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[t]));
+                            acc[t] = make_float2(sm.x, acc[t].y + sm.y);
+                        }
+                    }
+                    // value = acc 2^(Ey + Ex - 12): a power of two, applied to hi and lo
+                    const int ex = sEx[erow];
+                    const int e = Ey + (ex ? ex - 1022 : -1000) - 12;
+                    const float sc = (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.f;
+                    if (lane < 16 && eg < nm) {
+                        const int l0 = m + TC_CH * (cfirst + qe);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const int l = l0 + 2 * ((n0 + t) & 15) + es;
+                            if (l <= L) {
+                                float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
+                                *dst = make_float2(acc[t].x * sc, acc[t].y * sc);
+                            }
+                        }
+                    }
+                } else if (sp == 0) {
+                    atomicOr(A.status, 1);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+            }
+            if (q == nlive) break;
+            // ---- the 8 K-steps of chunk q into accumulator set st
+            const double *yb = ybuf + (size_t)st * TC_CH * TA_YS;
 #pragma unroll 1
             for (int kk = 0; kk < TC_T / 16; ++kk, ++gk) {
                 const int b = gk & 1;
-                unsigned char *a_b = sA + b * TC_S * W::A_KS;
+                unsigned char *yt = sY + b * TC_S * TA_BDIG;
                 // the MMAs of K-step gk - 2 read this buffer: wait (bounded) before rewriting it
                 if (gk >= 2 && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk >> 1) - 1) & 1))) ok = false;
-                uint32_t pk[TC_S][4];
-#pragma unroll
-                for (int t = 0; t < 8; t += 2) {
-                    float d0[TC_S], d1[TC_S];
-                    const int k0 = 16 * kk + 8 * kh + t;
-                    split_digits(yb[row * TA_YS + k0], Ey, d0);
-                    split_digits(yb[row * TA_YS + k0 + 1], Ey, d1);
-#pragma unroll
-                    for (int s = 0; s < TC_S; ++s)
-                        pk[s][t >> 1] = __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
-                }
-                if (kk == TC_T / 16 - 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TA_NT);  // y stage read
-                // A tile, K-major [64 x 16]: core matrix (row / 8, kh), row row % 8
-                const int off = (kh * (TA_CH / 8) + (row >> 3)) * 128 + (row & 7) * 16;
+                const double2 yy = *reinterpret_cast<const double2 *>(yb + jrow * TA_YS + 16 * kk + 8 * kh + 2 * kp);
+                float d0[TC_S], d1[TC_S];
+                split_digits(yy.x, Ey, d0);
+                split_digits(yy.y, Ey, d1);
+                if (kk == TC_T / 16 - 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TC_NT);  // y stage read
 #pragma unroll
                 for (int s = 0; s < TC_S; ++s)
-                    *(uint4 *)(a_b + s * W::A_KS + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+                    *(uint32_t *)(yt + s * TA_BDIG + boff) =
+                        __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
                 asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
-                ok = bar_red_and(BAR_SPLIT, TC_T, ok);
-                if (ok && lane == 0 && sp < 64) {  // sp 0: classes 0 .. NACC-2; sp 32: the merged last class
+                ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
+                if (ok && lane == 0 && w8 < 2) {  // warp 4: classes 0 .. NACC-2; warp 5: the merged last class
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const bool last_group = sp != 0;
-                    const uint32_t a0 = smem_u32(a_b), b0 = smem_u32(sB) + kk * 2 * (N / 8) * 128;
+                    const bool last_group = w8 == 1;
+                    const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * (TA_M / 8) * 128), b0 = smem_u32(yt);
+                    const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
 #pragma unroll
                     for (int w = 0; w <= TC_MAXW; ++w) {
-                        if ((w >= W::NACC - 1) != last_group) continue;
+                        if ((w >= TC_NACC - 1) != last_group) continue;
 #pragma unroll
                         for (int i = 0; i <= w; ++i) {
                             const int j = w - i;
-                            const int cls = w < W::NACC - 1 ? w : W::NACC - 1;
-                            const bool first = (kk == 0) && (i == 0) && (w <= W::NACC - 1);
-                            const uint64_t ad = umma_desc(a0 + i * W::A_KS, (TA_CH / 8) * 128, 128);
-                            const uint64_t bd = umma_desc(b0 + j * W::B_DIG, (N / 8) * 128, 128);
-                            umma_bf16(tmem + (uint32_t)(cls * N), ad, bd, idesc, first ? 0u : 1u);
+                            const int cls = w < TC_NACC - 1 ? w : TC_NACC - 1;
+                            const bool first = (kk == 0) && (i == 0) && (w <= TC_NACC - 1);
+                            const uint64_t ad = umma_desc(a0 + i * TA_ADIG, (TA_M / 8) * 128, 128);
+                            const uint64_t bd = umma_desc(b0 + j * TA_BDIG, (TC_CH / 8) * 128, 128);
+                            umma_bf16(dt + (uint32_t)(cls * TC_CH), ad, bd, idesc, first ? 0u : 1u);
                         }
                     }
                     umma_commit(&mbar[b]);
                 }
             }
-            // the chunk's last commits cover all its MMAs: wait (bounded), then read the accumulators
-            if (ok && !mbar_wait(&mbar[(gk - 1) & 1], (uint32_t)(((gk - 1) >> 1) & 1))) ok = false;
-            ok = bar_red_and(BAR_SPLIT, TC_T, ok);
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (ok) {
-                // rows 16 lw .. 16 lw + 15 in lanes 0-15 of this warp's quarter
-                float2 accv[N];
-#pragma unroll
-                for (int n = 0; n < N; ++n) accv[n] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int cls = 0; cls < W::NACC; ++cls) {
-#pragma unroll
-                    for (int n0 = 0; n0 < N; n0 += 16) {
-                        uint32_t v[16];
-                        const uint32_t addr = tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)(cls * N + n0);
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                            "[%16];"
-                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                              "=r"(v[14]), "=r"(v[15])
-                            : "r"(addr));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            // the digits carry their weights 2^(-7 s), so the classes add as they
-                            // are, in decreasing size: a double-float sum keeps them all
-                            const float2 sm = two_sum(accv[n0 + t].x, __uint_as_float(v[t]));
-                            accv[n0 + t] = make_float2(sm.x, accv[n0 + t].y + sm.y);
-                        }
-                    }
-                }
-                const int j = 16 * lw + lane;  // row = l - l0
-                const int l = m + TA_CH * c + j;
-                if (lane < 16 && l <= L) {
-                    const int h = ((l - m) & 1) * (N / 2);
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        if (g < A.nmaps) {
-                            float4 o;
-                            // value = acc 2^(Ey + Ex - 12): a power of two, applied to hi and lo
-                            const int er = Ey + (sEx[h + 2 * g] ? sEx[h + 2 * g] - 1022 : -1000) - 12;
-                            const int ei = Ey + (sEx[h + 2 * g + 1] ? sEx[h + 2 * g + 1] - 1022 : -1000) - 12;
-                            const float sr = (er >= -126 && er <= 127) ? __int_as_float((er + 127) << 23) : 0.f;
-                            const float si = (ei >= -126 && ei <= 127) ? __int_as_float((ei + 127) << 23) : 0.f;
-                            o.x = accv[h + 2 * g].x * sr;
-                            o.y = accv[h + 2 * g].y * sr;
-                            o.z = accv[h + 2 * g + 1].x * si;
-                            o.w = accv[h + 2 * g + 1].y * si;
-                            part[(int64_t)g * A.nalm + base + (l - m)] = o;
-                        }
-                    }
-                }
-            } else if (sp == 0) {
-                atomicOr(A.status, 1);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                                "r"(W::TMEM_COLS));
+                                "r"(TA_TMEM_COLS));
 }
 
 template <int N>
@@ -1079,27 +1036,35 @@ cudaError_t configure_tc_kernels()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc_synth_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcWs<16>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_anal_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TaWs<32>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_anal_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TaWs<16>::SMEM);
+        e = cudaFuncSetAttribute(tc_anal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TA_SMEM);
     return e;
 }
 
-// partial a_lm / c_lm per 128-slot block for one group of up to 8 maps (reduced per group)
+// index(mR + 1, mR + 1): the a_lm of m <= mR, which the Reinsch kernel covers on a polar block 0
+static int64_t polar_alm_count(const Plan &p)
+{
+    const int mR = p.polar_first_slot ? p.mR : -1;
+    return mR < 0 ? 0 : (int64_t)(mR + 1) * (2 * (int64_t)p.lmax + 3 - (mR + 1)) / 2;
+}
+
+// partial a_lm / c_lm per 128-slot block for one group of up to 16 maps (reduced per group),
+// [block][index][map] float4, then the Reinsch kernel's FP64 partials of polar block 0 for
+// m <= mR, [map][index] double2
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps)
 {
     const int nblk = (p.nslots + TC_T - 1) / TC_T;
-    return (size_t)nblk * (size_t)std::min(nmaps, TA_MAPS) * (size_t)p.nalm * sizeof(float4);
+    const size_t nm = (size_t)std::min(nmaps, TA_MAPS);
+    return (size_t)nblk * nm * (size_t)p.nalm * sizeof(float4) + nm * (size_t)polar_alm_count(p) * sizeof(double2);
 }
 
-// The precision-form analysis on the tensor cores: per group of up to 8 maps, the tensor-core
+// The precision-form analysis on the tensor cores: per group of up to 16 maps, the tensor-core
 // kernel for every non-polar slot block, the FP64 Reinsch kernel for block 0 when it is polar
 // (m <= mR), then the fixed-order block reduction into a_lm.
 cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch)
 {
     *nlaunch = 0;
-    TaArgs A{};
+    TcArgs A{};
     A.slotN = p.d_slotN;
     A.slotS = p.d_slotS;
     A.u = p.d_u;
@@ -1118,29 +1083,27 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
     A.mR = p.polar_first_slot ? p.mR : -1;
     A.nalm = p.nalm;
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    const int64_t fp64_lim = polar_alm_count(p);
     for (int g0 = 0; g0 < nmaps; g0 += TA_MAPS) {
         const int nm = std::min(TA_MAPS, nmaps - g0);
         A.nmaps = nm;
-        A.delta = delta + (int64_t)g0 * dstride;
+        A.delta = const_cast<double2 *>(delta) + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial;
-        const unsigned grid = (unsigned)((p.mmax + 1) * A.nblk);
-        if (nm > 4)
-            tc_anal_kernel<32><<<grid, TA_NT, TaWs<32>::SMEM, st>>>(A);
-        else
-            tc_anal_kernel<16><<<grid, TA_NT, TaWs<16>::SMEM, st>>>(A);
+        tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT, TA_SMEM, st>>>(A);
         ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        int64_t fp64_lim = 0;
-        if (A.mR >= 0) {
+        double2 *polar = nullptr;
+        if (fp64_lim > 0) {
             int n = 0;
-            e = launch_legendre_anal_polar(p, A.delta, (double2 *)partial, nm, TC_T, st, &n);
+            polar = (double2 *)(A.partial + (int64_t)A.nblk * nm * p.nalm);
+            e = launch_legendre_anal_polar(p, A.delta, polar, nm, TC_T, fp64_lim, st, &n);
             *nlaunch += n;
             if (e != cudaSuccess) return e;
-            fp64_lim = (int64_t)(A.mR + 1) * (2 * (int64_t)p.lmax + 3 - (A.mR + 1)) / 2;  // index(mR+1, mR+1)
         }
-        e = launch_reduce_blocks_df((const float4 *)partial, p.d_cfac, alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm, nm,
-                                    p.lmax, (int64_t)nm * p.nalm, fp64_lim, st);
+        // partial (block, map g, index i) at block * nalm nm + i nm + g
+        e = launch_reduce_blocks_df(A.partial, polar, fp64_lim, p.d_cfac, alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm,
+                                    nm, p.lmax, (int64_t)nm * p.nalm, 1, nm, fp64_lim, st);
         ++*nlaunch;
         if (e != cudaSuccess) return e;
     }

@@ -82,7 +82,7 @@ struct Plan {
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
     // launch tuning (sht_tune): maps or slots per thread per launch
-    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 0, 1};
+    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 1, 1};
 
     // workspace, grown on demand
     void *d_ws = nullptr;
@@ -127,18 +127,23 @@ cudaError_t build_phase_table(Plan &p);
 cudaError_t build_fft_tables(Plan &p);
 
 cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, double2 *partial, int nmaps, int slots,
-                                       cudaStream_t st, int *nlaunch);
+                                       int64_t map_stride, cudaStream_t st, int *nlaunch);
 int legendre_anal_df_nblk(const Plan &p);
 size_t legendre_anal_df_partial_bytes(const Plan &p, int nmaps);
 cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch);
 size_t tc_workspace_bytes(const Plan &p, int nmaps);
-// precision-form analysis on the tensor cores (groups of up to 8 maps, reduced per group)
+// precision-form analysis on the tensor cores (groups of up to 16 maps, reduced per group)
 cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch);
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps);
-cudaError_t launch_reduce_blocks_df(const float4 *partial, const double *cfac, double2 *alm, int nblk, int64_t nalm,
-                                    int nmaps, int lmax, int64_t blk_stride, int64_t fp64_lim, cudaStream_t st);
+// a_lm = c_lm * sum over blocks of double-float partials; partial (block, map, index) at
+// block * blk_stride + map * map_stride + index * idx_stride; for index < fp64_lim block 0 is
+// replaced by the FP64 partial polar[map * polar_stride + index]
+cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
+                                    const double *cfac, double2 *alm, int nblk, int64_t nalm, int nmaps, int lmax,
+                                    int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim,
+                                    cudaStream_t st);
 cudaError_t build_tc_scales(Plan &p);
 cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,
                                      cudaStream_t st, int *nlaunch);

@@ -215,7 +215,7 @@ class Plan:
             pass
 
     def set_mode(self, mode: int):
-        """MODE_FP64 (default) or MODE_SPLIT_BF16 (tensor-core contraction in the synthesis)."""
+        """MODE_FP64 (default) or MODE_SPLIT_BF16 (the precision form: tensor-core sums over l and rings)."""
         _check(load().sht_plan_set_mode(self._h, int(mode)), self._h, "sht_plan_set_mode")
 
     @property
