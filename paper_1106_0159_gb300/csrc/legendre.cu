@@ -599,63 +599,6 @@ cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, doubl
     return cudaSuccess;
 }
 
-// The Reinsch-form analysis CTAs only (slot block 0 of `slots` slots, m <= mR), writing FP64
-// partials of a_lm index i < index(mR + 1, mR + 1) for map g to partial[g * map_stride + i]
-// (block 0 of a [nblk][nmaps][nalm] buffer: map_stride = nalm).
-cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, double2 *partial, int nmaps, int slots,
-                                       int64_t map_stride, cudaStream_t st, int *nlaunch)
-{
-    *nlaunch = 0;
-    if (p.mR < 0 || !p.polar_first_slot) return cudaSuccess;
-    if (slots != 2 * ANA_T && slots != ANA_T) return cudaErrorInvalidValue;
-    AnaArgs A;
-    A.slotN = p.d_slotN;
-    A.slotS = p.d_slotS;
-    A.u = p.d_u;
-    A.s = p.d_s;
-    A.alpha = p.d_alpha;
-    A.cfac = p.d_cfac;
-    A.rein = p.d_rein;
-    A.mR = p.mR;
-    A.nslots = p.nslots;
-    A.nblk = 1;  // blockIdx.x = m, slot block 0
-    A.lmax = p.lmax;
-    A.mmax = p.mmax;
-    A.nrings = p.nrings;
-    A.nalm = p.nalm;
-    A.part_map_stride = map_stride;
-    A.part_blk_stride = 0;  // block 0 only
-    const unsigned grid = (unsigned)(p.mR + 1);
-    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
-    for (int g0 = 0; g0 < nmaps;) {
-        A.delta = delta + (int64_t)g0 * dstride;
-        A.partial = partial + (int64_t)g0 * map_stride;
-        if (nmaps - g0 >= 4) {  // the Reinsch recurrence (4 DFMA per step) runs once per launch
-            if (slots == ANA_T)
-                legendre_anal_kernel<4, 1><<<grid, ANA_T, 0, st>>>(A);
-            else
-                legendre_anal_kernel<4, 2><<<grid, ANA_T, 0, st>>>(A);
-            g0 += 4;
-        } else if (nmaps - g0 >= 2) {
-            if (slots == ANA_T)
-                legendre_anal_kernel<2, 1><<<grid, ANA_T, 0, st>>>(A);
-            else
-                legendre_anal_kernel<2, 2><<<grid, ANA_T, 0, st>>>(A);
-            g0 += 2;
-        } else {
-            if (slots == ANA_T)
-                legendre_anal_kernel<1, 1><<<grid, ANA_T, 0, st>>>(A);
-            else
-                legendre_anal_kernel<1, 2><<<grid, ANA_T, 0, st>>>(A);
-            g0 += 1;
-        }
-        ++*nlaunch;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 size_t legendre_anal_partial_bytes(const Plan &p, int nmaps)
 {
     const int per = anal_slots_per_cta(p);

@@ -20,9 +20,11 @@
 // double-float pair per component.  The fixed-order block reduction then
 // converts and sums the blocks in FP64.
 //
-// Polar slot blocks run the Reinsch form in the FP64 kernel (see legendre.cu);
-// here the first block of a polar plan is skipped for m <= mR and covered by
-// launch_legendre_anal_polar.
+// Polar slots (the first 256 slots of a plan whose first ring has sin(theta) < 0.03, for
+// m <= mR) run Reinsch's difference form of the recurrence in lambda itself (see legendre.cu:
+// four FP64 instructions per step instead of two) in the REIN instantiation of the same kernel,
+// which writes lambda-sums / c_lm in FP64 to a separate region that the block reduction reads in
+// place of those blocks.
 #include "sht_internal.h"
 
 #include <algorithm>
@@ -166,31 +168,38 @@ __device__ __forceinline__ void xor_permute(float2 v[DF_G], int b)
 struct DfArgs {
     const double2 *delta;  // [nmaps][nrings][mmax+1], first map of this group
     float4 *partial;       // [nblk][nmaps_total][nalm] as (re_hi, re_lo, im_hi, im_lo)
+    double2 *polar;        // Reinsch form: a_lm / c_lm of slots 0 .. 255 at [map * polar_stride + index]
+    int64_t polar_stride;
     const int *slotN, *slotS;
     const double *u, *s;
     const double *alpha, *cfac;
+    const double3 *rein;   // Reinsch coefficients (beta_l, rho_l, b0_l) for m <= mR
     int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
     int64_t nalm;
     int64_t part_blk_stride;  // nmaps_total * nalm
 };
 
-template <int N>
+__device__ __forceinline__ double widen_df(float2 a) { return (double)a.x + (double)a.y; }
+
+template <int N, bool REIN>
 struct DfSmem {
     float2 X[2][N][DF_T];           // [parity: Sigma, D][column][slot]
     float2 red[DF_T / 32][N][DF_CHL];  // [warp][column][l]: l contiguous, no bank conflicts
-    double al[DF_CHL];
+    double co[REIN ? 3 : 1][DF_CHL];   // y form: alpha_l; Reinsch form: beta_l, rho_l, b0_l
 };
 
-template <int N>
+// REIN = false: one CTA per (m, block of 256 slots), the y form, double-float partials.
+// REIN = true:  one CTA per m <= mR on slots 0 .. 255 (A.nblk = 1), Reinsch's form, FP64 partials.
+template <int N, bool REIN>
 __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DfSmem<N> &S = *reinterpret_cast<DfSmem<N> *>(smem_raw);
+    DfSmem<N, REIN> &S = *reinterpret_cast<DfSmem<N, REIN> *>(smem_raw);
 
     constexpr int NW = DF_T / 32;
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
-    if (m <= A.mR && A.s[blk * DF_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
+    if (!REIN && m <= A.mR && A.s[blk * DF_T] < POLAR_SIN) return;  // the REIN launch covers it
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int slot = blk * DF_T + tid;
     const bool active = slot < A.nslots;
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
         u = A.u[slot];
         double y0;
         sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
-        y2 = -y0;
+        y2 = REIN ? y0 : -y0;  // D_{m-1} = lambda_m (Reinsch) or y_{m-2} = -y_m, with y1 = 0
     }
     // Sigma and D of this slot, as double-float columns (2g: re, 2g+1: im)
     {
@@ -227,7 +236,16 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
     for (int l0 = m; l0 <= L; l0 += DF_CHL) {
         const int nl = min(DF_CHL, L - l0 + 1);
         __syncthreads();
-        if (tid < DF_CHL) S.al[tid] = (tid < nl) ? A.alpha[base + (l0 - m) + tid] : 0.0;
+        if (tid < DF_CHL) {
+            if (REIN) {
+                const double3 c = (tid < nl) ? A.rein[base + (l0 - m) + tid] : make_double3(0.0, 0.0, 0.0);
+                S.co[0][tid] = c.x;
+                S.co[1][tid] = c.y;
+                S.co[2][tid] = c.z;
+            } else {
+                S.co[0][tid] = (tid < nl) ? A.alpha[base + (l0 - m) + tid] : 0.0;
+            }
+        }
         __syncthreads();
         for (int j0 = 0; j0 < DF_CHL; j0 += DF_G) {
             // 8 recurrence steps (past the end: no-op steps with zero values)
@@ -239,10 +257,18 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
                 const int j = j0 + jj;
                 double y = 0.0;
                 if (j < nl) {
-                    const double t = fma(-u, y1, y1);
-                    y = fma(S.al[j], t, -y2);
-                    y2 = y1;
-                    y1 = y;
+                    if (REIN) {  // D_l = (1 + rho_l) D_{l-1} + g_l lambda_{l-1}, lambda_l = lambda_{l-1} + D_l
+                        const double g = fma(-S.co[0][j], u, S.co[2][j]);
+                        const double t = fma(g, y1, y2);
+                        y2 = fma(S.co[1][j], y2, t);
+                        y1 = y1 + y2;
+                        y = y1;
+                    } else {
+                        const double t = fma(-u, y1, y1);
+                        y = fma(S.co[0][j], t, -y2);
+                        y2 = y1;
+                        y1 = y;
+                    }
                 }
                 const bool use = active && j < nl && !(scaled && k < 0);
                 yv[jj] = use ? d2df(y) : make_float2(0.f, 0.f);
@@ -275,7 +301,8 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
             }
         }
         __syncthreads();
-        // add the warps, divide by c (the block reduction multiplies by it), write the block's partial
+        // add the warps and write the block's partial: y sums as double-float pairs (the block
+        // reduction multiplies by c_lm); Reinsch lambda sums divided by c_lm, in FP64
         for (int i = tid; i < nl * (N / 2); i += DF_T) {
             const int j = i % nl, g = i / nl;
             float2 re = S.red[0][2 * g][j], im = S.red[0][2 * g + 1][j];
@@ -285,8 +312,14 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
                 im = df_add(im, S.red[w][2 * g + 1][j]);
             }
             if (g < A.nmaps) {
-                A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.nalm + base + (l0 - m) + j] =
-                    make_float4(re.x, re.y, im.x, im.y);
+                const int64_t ix = base + (l0 - m) + j;
+                if (REIN) {
+                    const double c = A.cfac[ix];
+                    A.polar[(int64_t)g * A.polar_stride + ix] = make_double2(widen_df(re) / c, widen_df(im) / c);
+                } else {
+                    A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.nalm + ix] =
+                        make_float4(re.x, re.y, im.x, im.y);
+                }
             }
         }
     }
@@ -297,12 +330,11 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 // FP64-bound: four conversions and four adds per complex value and block) and the sum is widened
 // once.  Partial (block, map g, index i) sits at bk * blk_stride + g * map_stride + i * idx_stride:
 // [block][map][index] from the double-float kernel, [block][index][map] from the tensor-core one;
-// threads walk the innermost of the two.  For i < fp64_lim (m <= mR of a polar plan) the block-0
-// term is the Reinsch kernel's FP64 partial polar[g * polar_stride + i], split into hi + lo.
-__device__ __forceinline__ double widen_df(float2 a) { return (double)a.x + (double)a.y; }
-
+// threads walk the innermost of the two.  For i < fp64_lim (m <= mR of a polar plan) the Reinsch
+// kernel's FP64 partial polar[g * polar_stride + i], split into hi + lo, stands for blocks
+// 0 .. polar_blocks - 1.
 __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double2 *__restrict__ polar,
-                                        int64_t polar_stride, const double *__restrict__ cfac,
+                                        int64_t polar_stride, int polar_blocks, const double *__restrict__ cfac,
                                         double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
                                         int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim)
 {
@@ -319,17 +351,19 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
         }
         const float4 *src = partial + g * map_stride + i * idx_stride;
         float2 re, im;
+        int bk0 = 1;
         if (i < fp64_lim) {
             const double2 d = polar[g * polar_stride + i];
             re = d2df(d.x);
             im = d2df(d.y);
+            bk0 = polar_blocks;
         } else {
             const float4 v = src[0];
             re = make_float2(v.x, v.y);
             im = make_float2(v.z, v.w);
         }
 #pragma unroll 4
-        for (int bk = 1; bk < nblk; ++bk) {
+        for (int bk = bk0; bk < nblk; ++bk) {
             const float4 v = src[(int64_t)bk * blk_stride];
             re = df_add(re, make_float2(v.x, v.y));
             im = df_add(im, make_float2(v.z, v.w));
@@ -339,43 +373,98 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
     }
 }
 
-template <int N>
+template <int N, bool REIN>
 cudaError_t configure_df()
 {
-    const int smem = (int)sizeof(DfSmem<N>);
-    cudaError_t e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)sizeof(DfSmem<N, REIN>);
+    cudaError_t e =
+        cudaFuncSetAttribute(legendre_anal_df_kernel<N, REIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)  // all of the unified L1 as shared memory: as many CTAs per SM as it holds
-        e = cudaFuncSetAttribute(legendre_anal_df_kernel<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(legendre_anal_df_kernel<N, REIN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 
-template <int N>
+// grid: every (m, block) for the y form; m = 0 .. mR on block 0 for the Reinsch form
+template <int N, bool REIN>
 cudaError_t launch_df_group(const Plan &p, DfArgs A, cudaStream_t st)
 {
-    legendre_anal_df_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), DF_T, (int)sizeof(DfSmem<N>), st>>>(A);
+    const unsigned grid = REIN ? (unsigned)(A.mR + 1) : (unsigned)((p.mmax + 1) * A.nblk);
+    legendre_anal_df_kernel<N, REIN><<<grid, DF_T, (int)sizeof(DfSmem<N, REIN>), st>>>(A);
     return cudaGetLastError();
+}
+
+DfArgs df_args(const Plan &p)
+{
+    DfArgs A{};
+    A.slotN = p.d_slotN;
+    A.slotS = p.d_slotS;
+    A.u = p.d_u;
+    A.s = p.d_s;
+    A.alpha = p.d_alpha;
+    A.cfac = p.d_cfac;
+    A.rein = p.d_rein;
+    A.nslots = p.nslots;
+    A.nblk = (p.nslots + DF_T - 1) / DF_T;
+    A.lmax = p.lmax;
+    A.mmax = p.mmax;
+    A.nrings = p.nrings;
+    A.mR = p.polar_first_slot ? p.mR : -1;
+    A.nalm = p.nalm;
+    return A;
 }
 
 }  // namespace
 
 cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
-                                    const double *cfac, double2 *alm, int nblk, int64_t nalm, int nmaps, int lmax,
-                                    int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim,
-                                    cudaStream_t st)
+                                    int polar_blocks, const double *cfac, double2 *alm, int nblk, int64_t nalm,
+                                    int nmaps, int lmax, int64_t blk_stride, int64_t map_stride, int64_t idx_stride,
+                                    int64_t fp64_lim, cudaStream_t st)
 {
     const int64_t total = nalm * nmaps;
     const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, polar, polar_stride, cfac, alm, nblk, nalm, nmaps, lmax,
-                                                   blk_stride, map_stride, idx_stride, fp64_lim);
+    reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, polar, polar_stride, polar_blocks, cfac, alm, nblk, nalm,
+                                                   nmaps, lmax, blk_stride, map_stride, idx_stride, fp64_lim);
     return cudaGetLastError();
 }
 
 cudaError_t configure_df_kernels()
 {
-    cudaError_t e = configure_df<32>();
-    if (e == cudaSuccess) e = configure_df<16>();
-    if (e == cudaSuccess) e = configure_df<8>();
+    cudaError_t e = configure_df<32, false>();
+    if (e == cudaSuccess) e = configure_df<16, false>();
+    if (e == cudaSuccess) e = configure_df<8, false>();
+    if (e == cudaSuccess) e = configure_df<32, true>();
+    if (e == cudaSuccess) e = configure_df<16, true>();
+    if (e == cudaSuccess) e = configure_df<8, true>();
     return e;
+}
+
+int legendre_anal_df_polar_slots() { return DF_T; }
+
+// The Reinsch-form analysis of slots 0 .. 255 for m <= mR of a polar plan, in double-float:
+// a_lm / c_lm of map g at polar[g * polar_stride + index], index < index(mR + 1, mR + 1),
+// for groups of SHT_TUNE_DF_MAPS maps.
+cudaError_t launch_legendre_anal_df_polar(const Plan &p, const double2 *delta, double2 *polar, int64_t polar_stride,
+                                          int nmaps, cudaStream_t st, int *nlaunch)
+{
+    *nlaunch = 0;
+    DfArgs A = df_args(p);
+    if (A.mR < 0) return cudaSuccess;
+    A.nblk = 1;
+    A.polar_stride = polar_stride;
+    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    for (int g0 = 0; g0 < nmaps;) {
+        const int nm = std::min(p.tune[SHT_TUNE_DF_MAPS], nmaps - g0);
+        A.nmaps = nm;
+        A.delta = delta + (int64_t)g0 * dstride;
+        A.polar = polar + (int64_t)g0 * polar_stride;
+        cudaError_t e = nm > 8 ? launch_df_group<32, true>(p, A, st)
+                        : nm > 4 ? launch_df_group<16, true>(p, A, st)
+                                 : launch_df_group<8, true>(p, A, st);
+        ++*nlaunch;
+        if (e != cudaSuccess) return e;
+        g0 += nm;
+    }
+    return cudaSuccess;
 }
 
 int legendre_anal_df_nblk(const Plan &p) { return (p.nslots + DF_T - 1) / DF_T; }
@@ -385,26 +474,13 @@ size_t legendre_anal_df_partial_bytes(const Plan &p, int nmaps)
     return (size_t)legendre_anal_df_nblk(p) * (size_t)nmaps * (size_t)p.nalm * sizeof(float4);
 }
 
-// The precision-form analysis: double-float CTAs for every non-polar slot block, the FP64
-// Reinsch kernel for block 0 when it is polar (m <= mR), then the block reduction.
+// The precision-form analysis: double-float CTAs for every non-polar slot block, the Reinsch-form
+// CTAs for block 0 when it is polar (m <= mR), then the block reduction.
 cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch)
 {
     *nlaunch = 0;
-    DfArgs A{};
-    A.slotN = p.d_slotN;
-    A.slotS = p.d_slotS;
-    A.u = p.d_u;
-    A.s = p.d_s;
-    A.alpha = p.d_alpha;
-    A.cfac = p.d_cfac;
-    A.nslots = p.nslots;
-    A.nblk = legendre_anal_df_nblk(p);
-    A.lmax = p.lmax;
-    A.mmax = p.mmax;
-    A.nrings = p.nrings;
-    A.mR = p.polar_first_slot ? p.mR : -1;
-    A.nalm = p.nalm;
+    DfArgs A = df_args(p);
     A.part_blk_stride = (int64_t)nmaps * p.nalm;
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     int g0 = 0;
@@ -413,23 +489,24 @@ cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2
         A.nmaps = nm;
         A.delta = delta + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial + (int64_t)g0 * p.nalm;
-        cudaError_t e = nm > 8 ? launch_df_group<32>(p, A, st)
-                        : nm > 4 ? launch_df_group<16>(p, A, st)
-                                 : launch_df_group<8>(p, A, st);
+        cudaError_t e = nm > 8 ? launch_df_group<32, false>(p, A, st)
+                        : nm > 4 ? launch_df_group<16, false>(p, A, st)
+                                 : launch_df_group<8, false>(p, A, st);
         ++*nlaunch;
         if (e != cudaSuccess) return e;
         g0 += nm;
     }
     int64_t fp64_lim = 0;
-    if (A.mR >= 0) {  // FP64 partials in place of block 0 for m <= mR
+    if (A.mR >= 0) {  // FP64 partials in place of block 0 for m <= mR (16 bytes, as a float4)
         int n = 0;
-        cudaError_t e = launch_legendre_anal_polar(p, delta, (double2 *)partial, nmaps, DF_T, p.nalm, st, &n);
+        cudaError_t e = launch_legendre_anal_df_polar(p, delta, (double2 *)partial, p.nalm, nmaps, st, &n);
         *nlaunch += n;
         if (e != cudaSuccess) return e;
         fp64_lim = (int64_t)(A.mR + 1) * (2 * (int64_t)p.lmax + 3 - (A.mR + 1)) / 2;  // index(mR+1, mR+1)
     }
-    cudaError_t e = launch_reduce_blocks_df((const float4 *)partial, (const double2 *)partial, p.nalm, p.d_cfac, alm,
-                                            A.nblk, p.nalm, nmaps, p.lmax, A.part_blk_stride, p.nalm, 1, fp64_lim, st);
+    cudaError_t e = launch_reduce_blocks_df((const float4 *)partial, (const double2 *)partial, p.nalm, 1, p.d_cfac,
+                                            alm, A.nblk, p.nalm, nmaps, p.lmax, A.part_blk_stride, p.nalm, 1,
+                                            fp64_lim, st);
     ++*nlaunch;
     return e;
 }

@@ -250,6 +250,7 @@ struct TcArgs {
     float4 *partial;         // analysis: [nblk][nalm][nmaps] (re_hi, re_lo, im_hi, im_lo) of a_lm / c_lm per block
     int *status;             // device status word (bit 0: an mbarrier wait timed out)
     int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
+    int polar_slots;         // analysis: slots the Reinsch-form kernel covers for m <= mR (mR < 0: none)
     int64_t nalm;
 };
 
@@ -804,7 +805,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
 
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
-    if (m <= A.mR && A.s[blk * TC_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
+    if (m <= A.mR && blk * TC_T < A.polar_slots) return;  // the Reinsch-form kernel covers these slots
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool rec = warp < 4;
@@ -1048,7 +1049,7 @@ static int64_t polar_alm_count(const Plan &p)
 }
 
 // partial a_lm / c_lm per 128-slot block for one group of up to 16 maps (reduced per group),
-// [block][index][map] float4, then the Reinsch kernel's FP64 partials of polar block 0 for
+// [block][index][map] float4, then the Reinsch-form partials of the first polar slots for
 // m <= mR, [map][index] double2
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps)
 {
@@ -1058,8 +1059,8 @@ size_t tc_anal_partial_bytes(const Plan &p, int nmaps)
 }
 
 // The precision-form analysis on the tensor cores: per group of up to 16 maps, the tensor-core
-// kernel for every non-polar slot block, the FP64 Reinsch kernel for block 0 when it is polar
-// (m <= mR), then the fixed-order block reduction into a_lm.
+// kernel for every slot block outside the polar slots (m <= mR), the double-float Reinsch-form
+// kernel for those, then the fixed-order block reduction into a_lm.
 cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch)
 {
@@ -1081,6 +1082,8 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
     A.mmax = p.mmax;
     A.nrings = p.nrings;
     A.mR = p.polar_first_slot ? p.mR : -1;
+    A.polar_slots = legendre_anal_df_polar_slots();
+    static_assert(TC_T == 128, "the polar slots cover whole 128-slot blocks");
     A.nalm = p.nalm;
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     const int64_t fp64_lim = polar_alm_count(p);
@@ -1097,13 +1100,14 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
         if (fp64_lim > 0) {
             int n = 0;
             polar = (double2 *)(A.partial + (int64_t)A.nblk * nm * p.nalm);
-            e = launch_legendre_anal_polar(p, A.delta, polar, nm, TC_T, fp64_lim, st, &n);
+            e = launch_legendre_anal_df_polar(p, A.delta, polar, fp64_lim, nm, st, &n);
             *nlaunch += n;
             if (e != cudaSuccess) return e;
         }
         // partial (block, map g, index i) at block * nalm nm + i nm + g
-        e = launch_reduce_blocks_df(A.partial, polar, fp64_lim, p.d_cfac, alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm,
-                                    nm, p.lmax, (int64_t)nm * p.nalm, 1, nm, fp64_lim, st);
+        e = launch_reduce_blocks_df(A.partial, polar, fp64_lim, A.polar_slots / TC_T, p.d_cfac,
+                                    alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm, nm, p.lmax, (int64_t)nm * p.nalm, 1,
+                                    nm, fp64_lim, st);
         ++*nlaunch;
         if (e != cudaSuccess) return e;
     }

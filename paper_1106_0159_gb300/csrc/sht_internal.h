@@ -126,8 +126,6 @@ int ring_grid(const Plan &p);
 cudaError_t build_phase_table(Plan &p);
 cudaError_t build_fft_tables(Plan &p);
 
-cudaError_t launch_legendre_anal_polar(const Plan &p, const double2 *delta, double2 *partial, int nmaps, int slots,
-                                       int64_t map_stride, cudaStream_t st, int *nlaunch);
 int legendre_anal_df_nblk(const Plan &p);
 size_t legendre_anal_df_partial_bytes(const Plan &p, int nmaps);
 cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
@@ -138,12 +136,16 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
                                     cudaStream_t st, int *nlaunch);
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps);
 // a_lm = c_lm * sum over blocks of double-float partials; partial (block, map, index) at
-// block * blk_stride + map * map_stride + index * idx_stride; for index < fp64_lim block 0 is
-// replaced by the FP64 partial polar[map * polar_stride + index]
+// block * blk_stride + map * map_stride + index * idx_stride; for index < fp64_lim blocks
+// 0 .. polar_blocks - 1 are replaced by the FP64 partial polar[map * polar_stride + index]
 cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
-                                    const double *cfac, double2 *alm, int nblk, int64_t nalm, int nmaps, int lmax,
-                                    int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim,
-                                    cudaStream_t st);
+                                    int polar_blocks, const double *cfac, double2 *alm, int nblk, int64_t nalm,
+                                    int nmaps, int lmax, int64_t blk_stride, int64_t map_stride, int64_t idx_stride,
+                                    int64_t fp64_lim, cudaStream_t st);
+// precision-form Reinsch analysis of the first legendre_anal_df_polar_slots() slots for m <= mR
+int legendre_anal_df_polar_slots();
+cudaError_t launch_legendre_anal_df_polar(const Plan &p, const double2 *delta, double2 *polar, int64_t polar_stride,
+                                          int nmaps, cudaStream_t st, int *nlaunch);
 cudaError_t build_tc_scales(Plan &p);
 cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,
                                      cudaStream_t st, int *nlaunch);
