@@ -743,48 +743,53 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 // a_lm = c_lm sum over ring slots of y_lm(slot) X_m(slot), X = Sigma = Delta_N + Delta_S for even
 // l - m and X = D = Delta_N - Delta_S for odd (eq. almdef, Algorithm 5).  For one m and a block
 // of 128 slots this is the product [columns x slots] . [slots x l] (eq. matrix_vec transposed),
-// run on the tensor cores with the map columns as the MMA rows: M = 64 rows (Sigma and D, re and
+// run on the tensor cores with the map columns as the matrix rows: 64 rows (Sigma and D, re and
 // im, of up to 16 maps), K = 16 slots per MMA, N = 32 values of l (one 32-l chunk, its 16
 // even-parity values first).  Each row keeps the columns of its parity; the other half is
-// computed and dropped, which is cheap with the tensor pipe mostly idle.  The X digits of the
-// whole block (the A operand, 7 x 16 KB) are cut once per CTA and the y digits (B operand) per
-// K-step, so one launch serves 16 maps with one pass of the FP64 recurrence, which bounds it.
+// computed and dropped.  The X digits of the whole block (the A operand) are cut once per CTA and
+// the y digits (B operand) per K-step, so one launch serves 16 maps with one pass of the FP64
+// recurrence.
 //
-// Digits as in the synthesis: 7 balanced base-128 digits, products i + j <= 6 into five FP32
-// accumulators, y with the per-(m, block) exponent of tc_ymax_kernel and X with a per-(m, block,
-// row) exponent measured in the CTA.  Over 128 slots the class sums stay below 2^19 (exact in
-// FP32 for classes 0-3).  A chunk's accumulators (5 x 32 columns) are double-buffered in tensor
-// memory: the epilogue of chunk q - 1 runs while the MMAs of chunk q are issued.  It adds the
-// classes as double-float pairs (FP32 pipe) and writes the block's partial a_lm / c_lm,
-// [block][index][map], which the block reduction sums and multiplies by c_lm.
+// Digits as in the synthesis: 7 balanced base-128 digits of y (per-(m, block) exponent of
+// tc_ymax_kernel) and of X (per-(m, block, row) exponent measured in the CTA), products
+// i + j <= 6.  An MMA with 64 rows costs the tensor pipe as much as one with 128, so each MMA
+// stacks two X digits: A = [X_i ; X_(i+1)] (i even, X_7 = 0), rows 0-63 and 64-127, against one
+// y digit Y_j.  Its top half collects class i + j and its bottom half class i + j + 1, in the
+// accumulator region of t = i + j: regions t = 0 .. 4 alone, t = 5, 6 together.  That covers
+// all 28 products (and a few of class 7) with 16 MMAs per K-step instead of 28.  Over 128 slots
+// the class sums of regions 0-4 stay below 2^22, exact in FP32.  A chunk's six regions (6 x 32
+// columns) are double-buffered in tensor memory, so the epilogue of chunk q - 1 runs while the
+// MMAs of chunk q are issued.  It adds the classes as double-float pairs (FP32 pipe) and writes
+// the block's partial a_lm / c_lm, [block][index][map], which the block reduction sums and
+// multiplies by c_lm.
 //
 // CTA: one m, 128 slots, 384 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
 // 32 l); split warps 4-11 cut the y values of each K-step into the double-buffered B tiles, lane 0
-// of warps 4 and 5 issues the K-step's 28 MMAs (classes 0-3 / the merged class 4-6) and commits
-// them to the buffer's mbarrier, and all eight read the previous chunk's accumulators: with
-// M = 64, row r sits in lane 32 (r / 16) + r % 16 of tensor memory, so warps w and w + 4 share
-// one lane quarter and take 8 of its columns each.
+// of warps 4 and 5 issues the K-step's MMAs (regions 0-4: 9, regions 5-6: 7) and commits them to
+// the buffer's mbarrier, and all eight read the previous chunk's accumulators.  With 128 rows,
+// row r sits in tensor-memory lane r: lanes 0-63 hold the top halves and lanes 64-127 the bottom
+// halves of the same 64 rows, so the warps of lane quarters 2, 3 pass their sums to those of
+// quarters 0, 1 through shared memory.
 
-constexpr int TA_M = 64;                          // MMA rows: [Sigma | D] x 16 maps x (re, im)
+constexpr int TA_R = 64;                          // rows: [Sigma | D] x 16 maps x (re, im)
 constexpr int TA_MAPS = 16;                       // maps per launch
+constexpr int TA_XD = TC_S + 1;                   // X digits in shared memory (the last one zero)
+constexpr int TA_REG = 6;                         // accumulator regions per chunk
 constexpr int TA_YS = TC_T + 4;                   // y stage row stride (doubles): conflict-free pair loads
-constexpr int TA_ADIG = TA_M * TC_T * 2;          // one digit of the X operand [64 x 128 slots] bf16
+constexpr int TA_XBYTES = TA_XD * TA_R * TC_T * 2;  // X digits, [slot / 8][digit][row / 8] core matrices
+constexpr int TA_XKB = TA_XD * (TA_R / 8) * 128;  // bytes between 8-slot groups of the X operand
 constexpr int TA_BDIG = TC_CH * 16 * 2;           // one digit of a K-step's y tile [32 l x 16 slots] bf16
-constexpr int TA_ACC = TC_NACC * TC_CH;           // tensor-memory columns of one chunk's accumulators
-constexpr int TA_OFF_B = TC_S * TA_ADIG;
+constexpr int TA_ACC = TA_REG * TC_CH;            // tensor-memory columns of one chunk's accumulators
+constexpr int TA_OFF_B = TA_XBYTES;
 constexpr int TA_OFF_Y = TA_OFF_B + 2 * TC_S * TA_BDIG;
-constexpr int TA_OFF_E = TA_OFF_Y + 2 * TC_CH * TA_YS * 8;
-constexpr int TA_OFF_BAR = TA_OFF_E + TA_M * 4;
+constexpr int TA_OFF_X = TA_OFF_Y + 2 * TC_CH * TA_YS * 8;
+constexpr int TA_OFF_E = TA_OFF_X + TA_R * 16 * 8;
+constexpr int TA_OFF_BAR = TA_OFF_E + TA_R * 4;
 constexpr int TA_SMEM = TA_OFF_BAR + 64 + 1024;   // + alignment slack
 constexpr int TA_TMEM_COLS = 512;                 // two chunks of accumulators
 static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
 static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
-
-template <int M, int N>
-__device__ __forceinline__ uint32_t umma_idesc_mn()
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+static_assert(TC_S == 7 && TA_XD == 8, "the digit stacks pair digits 0-1, 2-3, 4-5, 6-7");
 
 __device__ __forceinline__ float2 two_sum(float a, float b)
 {
@@ -793,12 +798,43 @@ __device__ __forceinline__ float2 two_sum(float a, float b)
     return make_float2(s, (a - (s - bb)) + (b - bb));
 }
 
+// a + b for double-float pairs (TwoSum on the high parts)
+__device__ __forceinline__ float2 df_sum(float2 a, float2 b)
+{
+    const float2 s = two_sum(a.x, b.x);
+    return make_float2(s.x, s.y + a.y + b.y);
+}
+
+// the 8 columns n0 .. n0 + 7 of the 6 accumulator regions of chunk buffer tb, this warp's lanes,
+// summed over the regions as double-float pairs (regions in decreasing size)
+__device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int n0, float2 acc[8])
+{
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int reg = 0; reg < TA_REG; ++reg) {
+        uint32_t v[8];
+        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(tb * TA_ACC + reg * TC_CH + n0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7])
+                     : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[t]));
+            acc[t] = make_float2(sm.x, acc[t].y + sm.y);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sX = smem;                               // [digit][64 x 128] bf16, K-major (A operand)
+    unsigned char *sX = smem;                               // X digits (A operand), K-major
     unsigned char *sY = smem + TA_OFF_B;                    // [buffer][digit][32 x 16] bf16, K-major (B operand)
     double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
+    float2 *xch = (float2 *)(smem + TA_OFF_X);              // [64 rows][16 columns] bottom-half sums
     int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
     uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // [B buffer]
     uint32_t *tslot = (uint32_t *)(mbar + 2);
@@ -835,12 +871,12 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        // two issuing threads (class groups) commit to each B buffer's mbarrier
+        // two issuing threads (region groups) commit to each B buffer's mbarrier
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(2));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(2));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (tid < TA_M) sEx[tid] = 0;
+    if (tid < TA_R) sEx[tid] = 0;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -852,7 +888,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
     } else {
         // ------------------------------------------------ X digits, then split / MMA / epilogue
         const int Ey = A.Ey[m * A.nblk + blk];
-        const int hh = sp >> 7;  // this thread's maps: 8 hh .. 8 hh + 7 of slot r
+        const int hh = sp >> 7;  // this thread's maps: 8 hh .. 8 hh + 7 of slot r (uniform per warp)
         double xv[2][8][2];      // [Sigma, D][map][re, im] -> row 32 s + 2 g + c
         {
             const int rn = active ? A.slotN[slot] : -1, rs = active ? A.slotS[slot] : -1;
@@ -872,17 +908,24 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                 xv[1][gg][1] = dn.y - ds.y;
             }
         }
+        // row exponents: a warp's maximum first, then one shared atomic per row and warp
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int gg = 0; gg < 8; ++gg)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const int e = dexp(xv[s][gg][c]);
-                    if (e) atomicMax(&sEx[32 * s + 2 * (8 * hh + gg) + c], e);
+                    const unsigned e = __reduce_max_sync(0xffffffffu, (unsigned)dexp(xv[s][gg][c]));
+                    if (lane == 0 && e) atomicMax(&sEx[32 * s + 2 * (8 * hh + gg) + c], (int)e);
                 }
+        // the zero digit X_7 (the bottom half of the last stack)
+        for (int t = sp; t < TA_XBYTES / 16 / TA_XD; t += 2 * TC_T) {
+            const int kb = t / (TA_R / 8 * 8), rest = t - kb * (TA_R / 8 * 8);
+            *(uint4 *)(sX + kb * TA_XKB + (TC_S * (TA_R / 8)) * 128 + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
         bar_sync(BAR_SPLIT, 2 * TC_T);
-        // A operand, K-major [64 x 128]: element (row, k = r) in core matrix (row / 8, r / 8)
+        // A operand, K-major: element (row, k = r) of digit q in core matrix (q * 8 + row / 8) of
+        // 8-slot group r / 8, so that digits q and q + 1 form one 128-row operand
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -893,13 +936,13 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                     const int e = sEx[row];
                     float d[TC_S];
                     split_digits(xv[s][gg][c], e ? e - 1022 : -1000, d);
-                    const int off = ((r >> 3) * (TA_M / 8) + (row >> 3)) * 128 + (row & 7) * 16 + (r & 7) * 2;
+                    const int off = (r >> 3) * TA_XKB + (row >> 3) * 128 + (row & 7) * 16 + (r & 7) * 2;
 #pragma unroll
                     for (int q = 0; q < TC_S; ++q)
-                        *(__nv_bfloat16 *)(sX + q * TA_ADIG + off) = __float2bfloat16_rn(d[q]);
+                        *(__nv_bfloat16 *)(sX + off + q * (TA_R / 8) * 128) = __float2bfloat16_rn(d[q]);
                 }
 
-        const uint32_t idesc = umma_idesc_mn<TA_M, TC_CH>();
+        const uint32_t idesc = umma_idesc<TC_CH>();  // M = 128, N = 32
         const int w8 = warp - 4;  // 0..7
         // B tile element pair of this thread per K-step: row n (l - l0 = 2 (n % 16) + n / 16),
         // slots 2 kp, 2 kp + 1 of 8-slot half kh
@@ -907,12 +950,13 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
         const int n = 8 * nhi + nlo;
         const int jrow = 2 * (n & 15) + (n >> 4);
         const int boff = (kh * (TC_CH / 8) + nhi) * 128 + nlo * 16 + kp * 4;
-        // epilogue: lane quarter qd; rows 16 qd .. 16 qd + 15 are Sigma (qd < 2, even l - m) or D
-        // rows (odd), of maps 8 (qd & 1) + lane / 2, re or im by lane parity; columns n0 .. n0 + 7
+        // epilogue: lane quarter qd (warps w and w + 4 share one); row 32 (qd & 1) + lane, the top
+        // half (qd < 2) or the bottom half (qd >= 2) of its sums; Sigma rows (qd even) keep the even
+        // l - m columns 0-15, D rows the odd ones 16-31; this warp takes 8 of them from n0
         const int qd = warp & 3, hf = w8 >> 2;
-        const int erow = 16 * qd + (lane & 15);
-        const int es = qd >> 1;
-        const int eg = 8 * (qd & 1) + ((lane & 15) >> 1), ec = lane & 1;
+        const int es = qd & 1;
+        const int erow = 32 * es + lane;
+        const int eg = lane >> 1, ec = lane & 1;
         const int n0 = 16 * es + 8 * hf;
         int gk = 0;  // K-steps so far (all chunks)
         for (int q = 0; q <= nlive; ++q) {
@@ -924,45 +968,32 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                 if (ok && !mbar_wait(&mbar[gl & 1], (uint32_t)((gl >> 1) & 1))) ok = false;
                 ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                if (ok) {
-                    float2 acc[8];
+                float2 acc[8];
+                if (ok) read_regions(tmem, qd, tb, n0, acc);
+                if (ok && qd >= 2) {
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int cls = 0; cls < TC_NACC; ++cls) {
-                        uint32_t v[8];
-                        const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(tb * TA_ACC + cls * TC_CH + n0);
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                                       "=r"(v[6]), "=r"(v[7])
-                                     : "r"(addr));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;");
-                        // the digits carry their weights 2^(-7 s), so the classes add as they are, in
-                        // decreasing size: a double-float sum keeps them all
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[t]));
-                            acc[t] = make_float2(sm.x, acc[t].y + sm.y);
-                        }
-                    }
-                    // value = acc 2^(Ey + Ex - 12): a power of two, applied to hi and lo
+                    for (int t = 0; t < 8; ++t) xch[erow * 16 + 8 * hf + t] = acc[t];
+                }
+                bar_sync(BAR_SPLIT, 2 * TC_T);  // bottom sums in xch
+                if (ok && qd < 2) {
+                    // value = (top + bottom) 2^(Ey + Ex - 12): a power of two, applied to hi and lo
                     const int ex = sEx[erow];
                     const int e = Ey + (ex ? ex - 1022 : -1000) - 12;
                     const float sc = (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.f;
-                    if (lane < 16 && eg < nm) {
+                    if (eg < nm) {
                         const int l0 = m + TC_CH * (cfirst + qe);
 #pragma unroll
                         for (int t = 0; t < 8; ++t) {
+                            const float2 v = df_sum(acc[t], xch[erow * 16 + 8 * hf + t]);
                             const int l = l0 + 2 * ((n0 + t) & 15) + es;
                             if (l <= L) {
                                 float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
-                                *dst = make_float2(acc[t].x * sc, acc[t].y * sc);
+                                *dst = make_float2(v.x * sc, v.y * sc);
                             }
                         }
                     }
-                } else if (sp == 0) {
-                    atomicOr(A.status, 1);
                 }
+                if (!ok && sp == 0) atomicOr(A.status, 1);
                 asm volatile("tcgen05.fence::before_thread_sync;");
             }
             if (q == nlive) break;
@@ -986,22 +1017,21 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                 asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
-                if (ok && lane == 0 && w8 < 2) {  // warp 4: classes 0 .. NACC-2; warp 5: the merged last class
+                if (ok && lane == 0 && w8 < 2) {  // warp 4: regions 0-4; warp 5: regions 5-6
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const bool last_group = w8 == 1;
-                    const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * (TA_M / 8) * 128), b0 = smem_u32(yt);
+                    const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * TA_XKB), b0 = smem_u32(yt);
                     const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
 #pragma unroll
-                    for (int w = 0; w <= TC_MAXW; ++w) {
-                        if ((w >= TC_NACC - 1) != last_group) continue;
+                    for (int t = 0; t <= TC_MAXW; ++t) {
+                        if ((t >= TA_REG - 1) != (w8 == 1)) continue;
+                        const int reg = t < TA_REG - 1 ? t : TA_REG - 1;
 #pragma unroll
-                        for (int i = 0; i <= w; ++i) {
-                            const int j = w - i;
-                            const int cls = w < TC_NACC - 1 ? w : TC_NACC - 1;
-                            const bool first = (kk == 0) && (i == 0) && (w <= TC_NACC - 1);
-                            const uint64_t ad = umma_desc(a0 + i * TA_ADIG, (TA_M / 8) * 128, 128);
+                        for (int i = 0; i <= t; i += 2) {  // stack [X_i ; X_(i+1)] against Y_(t - i)
+                            const int j = t - i;
+                            const bool first = (kk == 0) && (i == 0) && (t <= TA_REG - 1);
+                            const uint64_t ad = umma_desc(a0 + i * (TA_R / 8) * 128, TA_XKB, 128);
                             const uint64_t bd = umma_desc(b0 + j * TA_BDIG, (TC_CH / 8) * 128, 128);
-                            umma_bf16(dt + (uint32_t)(cls * TC_CH), ad, bd, idesc, first ? 0u : 1u);
+                            umma_bf16(dt + (uint32_t)(reg * TC_CH), ad, bd, idesc, first ? 0u : 1u);
                         }
                     }
                     umma_commit(&mbar[b]);
