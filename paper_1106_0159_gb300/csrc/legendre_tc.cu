@@ -752,20 +752,21 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 //
 // Digits as in the synthesis: 7 balanced base-128 digits of y (per-(m, block) exponent of
 // tc_ymax_kernel) and of X (per-(m, block, row) exponent measured in the CTA), products
-// i + j <= 6.  An MMA with 64 rows costs the tensor pipe as much as one with 128, so each MMA
-// stacks two X digits: A = [X_i ; X_(i+1)] (i even, X_7 = 0), rows 0-63 and 64-127, against one
-// y digit Y_j.  Its top half collects class i + j and its bottom half class i + j + 1, in the
-// accumulator region of t = i + j: regions t = 0 .. 4 alone, t = 5, 6 together.  That covers
-// all 28 products (and a few of class 7) with 16 MMAs per K-step instead of 28.  Over 128 slots
-// the class sums of regions 0-4 stay below 2^22, exact in FP32.  A chunk's six regions (6 x 32
-// columns) are double-buffered in tensor memory, so the epilogue of chunk q - 1 runs while the
-// MMAs of chunk q are issued.  It adds the classes as double-float pairs (FP32 pipe) and writes
-// the block's partial a_lm / c_lm, [block][index][map], which the block reduction sums and
-// multiplies by c_lm.
+// i + j <= 6.  A tcgen05 MMA of 64 rows costs as much as one of 128, and N = 64 about as much as
+// N = 32 (measured: 46 and 48 cycles), so each MMA stacks two digits on both sides:
+// A = [X_a ; X_(a+1)] (rows 0-63, 64-127) and B = [Y_b | Y_(b+1)] (columns 0-31, 32-63), a and b
+// even, X_7 = Y_7 = 0.  Its four quadrants collect classes a + b, a + b + 1 (two) and a + b + 2,
+// in the accumulator region of t = a + b (0, 2, 4, 6).  The ten MMAs with a + b <= 6 cover all
+// 28 products (and some of classes 7 and 8) instead of 28 MMAs, and every quadrant holds one
+// class: over 128 slots its sum stays below 2^22, exact in FP32.  A chunk's four regions
+// (4 x 64 columns) are double-buffered in tensor memory, so the epilogue of chunk q - 1 runs
+// while the MMAs of chunk q are issued.  It adds the quadrants as double-float pairs (FP32 pipe)
+// and writes the block's partial a_lm / c_lm, [block][index][map], which the block reduction
+// sums and multiplies by c_lm.
 //
 // CTA: one m, 128 slots, 384 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
 // 32 l); split warps 4-11 cut the y values of each K-step into the double-buffered B tiles, lane 0
-// of warps 4 and 5 issues the K-step's MMAs (regions 0-4: 9, regions 5-6: 7) and commits them to
+// of warps 4 and 5 issues the K-step's MMAs (regions 0-4: 6, region 6: 4) and commits them to
 // the buffer's mbarrier, and all eight read the previous chunk's accumulators.  With 128 rows,
 // row r sits in tensor-memory lane r: lanes 0-63 hold the top halves and lanes 64-127 the bottom
 // halves of the same 64 rows, so the warps of lane quarters 2, 3 pass their sums to those of
@@ -773,15 +774,18 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 
 constexpr int TA_R = 64;                          // rows: [Sigma | D] x 16 maps x (re, im)
 constexpr int TA_MAPS = 16;                       // maps per launch
-constexpr int TA_XD = TC_S + 1;                   // X digits in shared memory (the last one zero)
-constexpr int TA_REG = 6;                         // accumulator regions per chunk
+constexpr int TA_XD = TC_S + 1;                   // digits of X and of y in shared memory (the last one zero)
+constexpr int TA_REG = 4;                         // accumulator regions per chunk (t = 0, 2, 4, 6)
+constexpr int TA_N = 2 * TC_CH;                   // MMA N: two y digits of one 32-l chunk
 constexpr int TA_YS = TC_T + 4;                   // y stage row stride (doubles): conflict-free pair loads
 constexpr int TA_XBYTES = TA_XD * TA_R * TC_T * 2;  // X digits, [slot / 8][digit][row / 8] core matrices
 constexpr int TA_XKB = TA_XD * (TA_R / 8) * 128;  // bytes between 8-slot groups of the X operand
-constexpr int TA_BDIG = TC_CH * 16 * 2;           // one digit of a K-step's y tile [32 l x 16 slots] bf16
-constexpr int TA_ACC = TA_REG * TC_CH;            // tensor-memory columns of one chunk's accumulators
+constexpr int TA_BDIG = (TC_CH / 8) * 128;        // one digit of one 8-slot group of a K-step's y tile
+constexpr int TA_BKB = TA_XD * TA_BDIG;           // bytes between the two 8-slot groups of a y tile
+constexpr int TA_BTILE = 2 * TA_BKB;              // one K-step's y tile, [slot / 8][digit][l / 8] core matrices
+constexpr int TA_ACC = TA_REG * TA_N;             // tensor-memory columns of one chunk's accumulators
 constexpr int TA_OFF_B = TA_XBYTES;
-constexpr int TA_OFF_Y = TA_OFF_B + 2 * TC_S * TA_BDIG;
+constexpr int TA_OFF_Y = TA_OFF_B + 2 * TA_BTILE;
 constexpr int TA_OFF_X = TA_OFF_Y + 2 * TC_CH * TA_YS * 8;
 constexpr int TA_OFF_E = TA_OFF_X + TA_R * 16 * 8;
 constexpr int TA_OFF_BAR = TA_OFF_E + TA_R * 4;
@@ -790,6 +794,7 @@ constexpr int TA_TMEM_COLS = 512;                 // two chunks of accumulators
 static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
 static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
 static_assert(TC_S == 7 && TA_XD == 8, "the digit stacks pair digits 0-1, 2-3, 4-5, 6-7");
+static_assert(TC_MAXW == 6, "regions t = 0, 2, 4, 6 cover the products of classes up to 6");
 
 __device__ __forceinline__ float2 two_sum(float a, float b)
 {
@@ -805,16 +810,19 @@ __device__ __forceinline__ float2 df_sum(float2 a, float2 b)
     return make_float2(s.x, s.y + a.y + b.y);
 }
 
-// the 8 columns n0 .. n0 + 7 of the 6 accumulator regions of chunk buffer tb, this warp's lanes,
-// summed over the regions as double-float pairs (regions in decreasing size)
+// columns n0 .. n0 + 7 and 32 + n0 .. 32 + n0 + 7 (the two y-digit halves) of the 4 accumulator
+// regions of chunk buffer tb, this warp's lanes, summed as double-float pairs (classes roughly in
+// decreasing size)
 __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int n0, float2 acc[8])
 {
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int reg = 0; reg < TA_REG; ++reg) {
+    for (int h = 0; h < 2 * TA_REG; ++h) {
+        const int reg = h >> 1, half = h & 1;
         uint32_t v[8];
-        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(tb * TA_ACC + reg * TC_CH + n0);
+        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) +
+                              (uint32_t)(tb * TA_ACC + reg * TA_N + half * TC_CH + n0);
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                        "=r"(v[7])
@@ -832,7 +840,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sX = smem;                               // X digits (A operand), K-major
-    unsigned char *sY = smem + TA_OFF_B;                    // [buffer][digit][32 x 16] bf16, K-major (B operand)
+    unsigned char *sY = smem + TA_OFF_B;                    // [buffer] y digit tiles, K-major (B operand)
     double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
     float2 *xch = (float2 *)(smem + TA_OFF_X);              // [64 rows][16 columns] bottom-half sums
     int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
@@ -918,10 +926,14 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                     const unsigned e = __reduce_max_sync(0xffffffffu, (unsigned)dexp(xv[s][gg][c]));
                     if (lane == 0 && e) atomicMax(&sEx[32 * s + 2 * (8 * hh + gg) + c], (int)e);
                 }
-        // the zero digit X_7 (the bottom half of the last stack)
+        // the zero digits X_7 and Y_7 (the second halves of the last stacks)
         for (int t = sp; t < TA_XBYTES / 16 / TA_XD; t += 2 * TC_T) {
             const int kb = t / (TA_R / 8 * 8), rest = t - kb * (TA_R / 8 * 8);
             *(uint4 *)(sX + kb * TA_XKB + (TC_S * (TA_R / 8)) * 128 + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (sp < 2 * 2 * TA_BDIG / 16) {  // [buffer][8-slot group]
+            const int g2 = sp / (TA_BDIG / 16), rest = sp - g2 * (TA_BDIG / 16);
+            *(uint4 *)(sY + g2 * TA_BKB + TC_S * TA_BDIG + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
         }
         bar_sync(BAR_SPLIT, 2 * TC_T);
         // A operand, K-major: element (row, k = r) of digit q in core matrix (q * 8 + row / 8) of
@@ -942,14 +954,14 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                         *(__nv_bfloat16 *)(sX + off + q * (TA_R / 8) * 128) = __float2bfloat16_rn(d[q]);
                 }
 
-        const uint32_t idesc = umma_idesc<TC_CH>();  // M = 128, N = 32
+        const uint32_t idesc = umma_idesc<TA_N>();  // M = 128, N = 64
         const int w8 = warp - 4;  // 0..7
         // B tile element pair of this thread per K-step: row n (l - l0 = 2 (n % 16) + n / 16),
         // slots 2 kp, 2 kp + 1 of 8-slot half kh
         const int kp = lane & 3, nlo = lane >> 2, nhi = w8 & 3, kh = w8 >> 2;
         const int n = 8 * nhi + nlo;
         const int jrow = 2 * (n & 15) + (n >> 4);
-        const int boff = (kh * (TC_CH / 8) + nhi) * 128 + nlo * 16 + kp * 4;
+        const int boff = kh * TA_BKB + nhi * 128 + nlo * 16 + kp * 4;
         // epilogue: lane quarter qd (warps w and w + 4 share one); row 32 (qd & 1) + lane, the top
         // half (qd < 2) or the bottom half (qd >= 2) of its sums; Sigma rows (qd even) keep the even
         // l - m columns 0-15, D rows the odd ones 16-31; this warp takes 8 of them from n0
@@ -1002,7 +1014,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
 #pragma unroll 1
             for (int kk = 0; kk < TC_T / 16; ++kk, ++gk) {
                 const int b = gk & 1;
-                unsigned char *yt = sY + b * TC_S * TA_BDIG;
+                unsigned char *yt = sY + b * TA_BTILE;
                 // the MMAs of K-step gk - 2 read this buffer: wait (bounded) before rewriting it
                 if (gk >= 2 && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk >> 1) - 1) & 1))) ok = false;
                 const double2 yy = *reinterpret_cast<const double2 *>(yb + jrow * TA_YS + 16 * kk + 8 * kh + 2 * kp);
@@ -1017,21 +1029,19 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                 asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
-                if (ok && lane == 0 && w8 < 2) {  // warp 4: regions 0-4; warp 5: regions 5-6
+                if (ok && lane == 0 && w8 < 2) {  // warp 4: regions t = 0, 2, 4; warp 5: region t = 6
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * TA_XKB), b0 = smem_u32(yt);
                     const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
 #pragma unroll
-                    for (int t = 0; t <= TC_MAXW; ++t) {
-                        if ((t >= TA_REG - 1) != (w8 == 1)) continue;
-                        const int reg = t < TA_REG - 1 ? t : TA_REG - 1;
+                    for (int t = 0; t <= TC_MAXW; t += 2) {
+                        if ((t == TC_MAXW) != (w8 == 1)) continue;
 #pragma unroll
-                        for (int i = 0; i <= t; i += 2) {  // stack [X_i ; X_(i+1)] against Y_(t - i)
+                        for (int i = 0; i <= t; i += 2) {  // [X_i ; X_(i+1)] against [Y_(t-i) | Y_(t-i+1)]
                             const int j = t - i;
-                            const bool first = (kk == 0) && (i == 0) && (t <= TA_REG - 1);
                             const uint64_t ad = umma_desc(a0 + i * (TA_R / 8) * 128, TA_XKB, 128);
-                            const uint64_t bd = umma_desc(b0 + j * TA_BDIG, (TC_CH / 8) * 128, 128);
-                            umma_bf16(dt + (uint32_t)(reg * TC_CH), ad, bd, idesc, first ? 0u : 1u);
+                            const uint64_t bd = umma_desc(b0 + j * TA_BDIG, TA_BKB, 128);
+                            umma_bf16(dt + (uint32_t)((t / 2) * TA_N), ad, bd, idesc, (kk == 0 && i == 0) ? 0u : 1u);
                         }
                     }
                     umma_commit(&mbar[b]);
