@@ -764,13 +764,14 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 // and writes the block's partial a_lm / c_lm, [block][index][map], which the block reduction
 // sums and multiplies by c_lm.
 //
-// CTA: one m, 128 slots, 384 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
-// 32 l); split warps 4-11 cut the y values of each K-step into the double-buffered B tiles, lane 0
-// of warps 4 and 5 issues the K-step's MMAs (regions 0-4: 6, region 6: 4) and commits them to
-// the buffer's mbarrier, and all eight read the previous chunk's accumulators.  With 128 rows,
-// row r sits in tensor-memory lane r: lanes 0-63 hold the top halves and lanes 64-127 the bottom
-// halves of the same 64 rows, so the warps of lane quarters 2, 3 pass their sums to those of
-// quarters 0, 1 through shared memory.
+// CTA: one m, 128 slots, 416 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
+// 32 l).  Split warps 4-11 cut the y values of each K-step into the double-buffered y tiles and
+// signal each tile's full barrier; lane 0 of warp 12 waits for it, issues the K-step's 10 MMAs and
+// commits them to the buffer's done barrier, so the split never waits for MMA issue.  The split
+// warps also read the previous chunk's accumulators (and release them to the issuer through the
+// set's free barrier).  With 128 rows, row r sits in tensor-memory lane r: lanes 0-63 hold the top
+// halves and lanes 64-127 the bottom halves of the same 64 rows, so the warps of lane quarters
+// 2, 3 pass their sums to those of quarters 0, 1 through shared memory.
 
 constexpr int TA_R = 64;                          // rows: [Sigma | D] x 16 maps x (re, im)
 constexpr int TA_MAPS = 16;                       // maps per launch
@@ -791,6 +792,7 @@ constexpr int TA_OFF_E = TA_OFF_X + TA_R * 16 * 8;
 constexpr int TA_OFF_BAR = TA_OFF_E + TA_R * 4;
 constexpr int TA_SMEM = TA_OFF_BAR + 64 + 1024;   // + alignment slack
 constexpr int TA_TMEM_COLS = 512;                 // two chunks of accumulators
+constexpr int TA_NT = TC_NT + 32;                 // 4 recurrence + 8 split warps + 1 MMA-issuing warp
 static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
 static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
 static_assert(TC_S == 7 && TA_XD == 8, "the digit stacks pair digits 0-1, 2-3, 4-5, 6-7");
@@ -836,7 +838,7 @@ __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb,
     }
 }
 
-__global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
+__global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sX = smem;                               // X digits (A operand), K-major
@@ -844,15 +846,17 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
     double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
     float2 *xch = (float2 *)(smem + TA_OFF_X);              // [64 rows][16 columns] bottom-half sums
     int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
-    uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // [B buffer]
-    uint32_t *tslot = (uint32_t *)(mbar + 2);
+    uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // done[2] (MMAs of a B buffer complete),
+    uint64_t *full = mbar + 2;                              // full[2] (a B buffer written),
+    uint64_t *tfree = mbar + 4;                             // tfree[2] (an accumulator set read out)
+    uint32_t *tslot = (uint32_t *)(mbar + 6);
 
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
     if (m <= A.mR && blk * TC_T < A.polar_slots) return;  // the Reinsch-form kernel covers these slots
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool rec = warp < 4;
+    const bool rec = warp < 4, issuer = warp == TA_NT / 32 - 1;
     const int sp = tid - TC_T;                              // split-thread index 0..255
     const int r = rec ? tid : (sp & (TC_T - 1));            // slot within the block
     const int slot = blk * TC_T + r;
@@ -869,7 +873,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
     {
         const int64_t dead = (int64_t)min(TC_CH * cfirst, L - m + 1) * nm;
         float4 *p0 = part + base * nm;
-        for (int64_t t = tid; t < dead; t += TC_NT) p0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t t = tid; t < dead; t += TA_NT) p0[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (nlive <= 0) return;
 
@@ -879,9 +883,11 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        // two issuing threads (region groups) commit to each B buffer's mbarrier
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(2));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(2));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[i])), "r"(1));          // commit
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(2 * TC_T));   // split threads
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfree[i])), "r"(2 * TC_T));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (tid < TA_R) sEx[tid] = 0;
@@ -893,8 +899,44 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
     bool ok = true;
     if (rec) {
         recurrence_warps<TA_YS>(A, m, blk, r, active, base, nch, cfirst, ybuf);
+    } else if (issuer) {
+        // ------------------------------------------------ MMA issue (lane 0 of the last warp)
+        // per chunk q: wait until accumulator set q & 1 is read out (chunk q - 2), then per K-step
+        // until its y tile is written, issue its 10 MMAs and commit them to the buffer's done barrier
+        const uint32_t idesc = umma_idesc<TA_N>();  // M = 128, N = 64
+        for (int q = 0; q < nlive; ++q) {
+            const int st = q & 1;
+            if (lane == 0 && q >= 2 && ok && !mbar_wait(&tfree[st], (uint32_t)(((q - 2) >> 1) & 1))) ok = false;
+#pragma unroll 1
+            for (int kk = 0; kk < TC_T / 16; ++kk) {
+                const int gk = 8 * q + kk, b = gk & 1;
+                if (lane == 0) {
+                    if (ok && !mbar_wait(&full[b], (uint32_t)((gk >> 1) & 1))) ok = false;
+                    if (ok) {
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * TA_XKB);
+                        const uint32_t b0 = smem_u32(sY + b * TA_BTILE);
+                        const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
+#pragma unroll
+                        for (int t = 0; t <= TC_MAXW; t += 2) {
+#pragma unroll
+                            for (int i = 0; i <= t; i += 2) {  // [X_i ; X_(i+1)] against [Y_(t-i) | Y_(t-i+1)]
+                                const int j = t - i;
+                                const uint64_t ad = umma_desc(a0 + i * (TA_R / 8) * 128, TA_XKB, 128);
+                                const uint64_t bd = umma_desc(b0 + j * TA_BDIG, TA_BKB, 128);
+                                umma_bf16(dt + (uint32_t)((t / 2) * TA_N), ad, bd, idesc,
+                                          (kk == 0 && i == 0) ? 0u : 1u);
+                            }
+                        }
+                        umma_commit(&mbar[b]);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0 && !ok) atomicOr(A.status, 1);
     } else {
-        // ------------------------------------------------ X digits, then split / MMA / epilogue
+        // ------------------------------------------------ X digits, then split / epilogue
         const int Ey = A.Ey[m * A.nblk + blk];
         const int hh = sp >> 7;  // this thread's maps: 8 hh .. 8 hh + 7 of slot r (uniform per warp)
         double xv[2][8][2];      // [Sigma, D][map][re, im] -> row 32 s + 2 g + c
@@ -954,9 +996,8 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                         *(__nv_bfloat16 *)(sX + off + q * (TA_R / 8) * 128) = __float2bfloat16_rn(d[q]);
                 }
 
-        const uint32_t idesc = umma_idesc<TA_N>();  // M = 128, N = 64
         const int w8 = warp - 4;  // 0..7
-        // B tile element pair of this thread per K-step: row n (l - l0 = 2 (n % 16) + n / 16),
+        // y tile element pair of this thread per K-step: row n (l - l0 = 2 (n % 16) + n / 16),
         // slots 2 kp, 2 kp + 1 of 8-slot half kh
         const int kp = lane & 3, nlo = lane >> 2, nhi = w8 & 3, kh = w8 >> 2;
         const int n = 8 * nhi + nlo;
@@ -970,18 +1011,19 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
         const int erow = 32 * es + lane;
         const int eg = lane >> 1, ec = lane & 1;
         const int n0 = 16 * es + 8 * hf;
-        int gk = 0;  // K-steps so far (all chunks)
         for (int q = 0; q <= nlive; ++q) {
             const int st = q & 1;
             if (q < nlive) bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
             if (q >= 1) {
-                // ---- epilogue of chunk q - 1: its last commit covers all its MMAs
-                const int qe = q - 1, tb = qe & 1, gl = gk - 1;
+                // ---- epilogue of chunk q - 1: the commit of its last K-step covers all its MMAs
+                const int qe = q - 1, tb = qe & 1, gl = 8 * qe + 7;
                 if (ok && !mbar_wait(&mbar[gl & 1], (uint32_t)((gl >> 1) & 1))) ok = false;
-                ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-wide
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 float2 acc[8];
                 if (ok) read_regions(tmem, qd, tb, n0, acc);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[tb])) : "memory");
                 if (ok && qd >= 2) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) xch[erow * 16 + 8 * hf + t] = acc[t];
@@ -1005,15 +1047,13 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                         }
                     }
                 }
-                if (!ok && sp == 0) atomicOr(A.status, 1);
-                asm volatile("tcgen05.fence::before_thread_sync;");
             }
             if (q == nlive) break;
-            // ---- the 8 K-steps of chunk q into accumulator set st
+            // ---- the 8 y tiles of chunk q
             const double *yb = ybuf + (size_t)st * TC_CH * TA_YS;
 #pragma unroll 1
-            for (int kk = 0; kk < TC_T / 16; ++kk, ++gk) {
-                const int b = gk & 1;
+            for (int kk = 0; kk < TC_T / 16; ++kk) {
+                const int gk = 8 * q + kk, b = gk & 1;
                 unsigned char *yt = sY + b * TA_BTILE;
                 // the MMAs of K-step gk - 2 read this buffer: wait (bounded) before rewriting it
                 if (gk >= 2 && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk >> 1) - 1) & 1))) ok = false;
@@ -1027,27 +1067,10 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_anal_kernel(TcArgs A)
                     *(uint32_t *)(yt + s * TA_BDIG + boff) =
                         __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
                 asm volatile("fence.proxy.async.shared::cta;");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                ok = bar_red_and(BAR_SPLIT, 2 * TC_T, ok);
-                if (ok && lane == 0 && w8 < 2) {  // warp 4: regions t = 0, 2, 4; warp 5: region t = 6
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * TA_XKB), b0 = smem_u32(yt);
-                    const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
-#pragma unroll
-                    for (int t = 0; t <= TC_MAXW; t += 2) {
-                        if ((t == TC_MAXW) != (w8 == 1)) continue;
-#pragma unroll
-                        for (int i = 0; i <= t; i += 2) {  // [X_i ; X_(i+1)] against [Y_(t-i) | Y_(t-i+1)]
-                            const int j = t - i;
-                            const uint64_t ad = umma_desc(a0 + i * (TA_R / 8) * 128, TA_XKB, 128);
-                            const uint64_t bd = umma_desc(b0 + j * TA_BDIG, TA_BKB, 128);
-                            umma_bf16(dt + (uint32_t)((t / 2) * TA_N), ad, bd, idesc, (kk == 0 && i == 0) ? 0u : 1u);
-                        }
-                    }
-                    umma_commit(&mbar[b]);
-                }
+                asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
             }
         }
+        if (!ok && (tid & 31) == 0) atomicOr(A.status, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -1132,7 +1155,7 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
         A.nmaps = nm;
         A.delta = const_cast<double2 *>(delta) + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial;
-        tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT, TA_SMEM, st>>>(A);
+        tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TA_NT, TA_SMEM, st>>>(A);
         ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
