@@ -208,6 +208,34 @@ __device__ __forceinline__ void umma_commit(uint64_t *mbar)
         smem_u32(mbar)));
 }
 
+// 1 in one lane of the (converged) warp, 0 in the others
+__device__ __forceinline__ uint32_t elect_one()
+{
+    uint32_t e;
+    asm volatile("{\n .reg .pred p;\n .reg .b32 r;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(e));
+    return e;
+}
+
+// the MMA and the commit issued by the lane with issue != 0 while the whole warp runs the code, so
+// that descriptors and addresses stay warp-uniform
+__device__ __forceinline__ void umma_bf16_by(uint32_t issue, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 q, %5, 0;\n"
+        " @q tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(issue));
+}
+
+__device__ __forceinline__ void umma_commit_by(uint32_t issue, uint64_t *mbar)
+{
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.b32 q, %1, 0;\n"
+        " @q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(smem_u32(mbar)),
+        "r"(issue));
+}
+
 // bounded wait for completion of the given phase parity; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
 {
@@ -766,8 +794,8 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
 //
 // CTA: one m, 128 slots, 416 threads.  Warps 0-3 run the recurrence (recurrence_warps, y stage of
 // 32 l).  Split warps 4-11 cut the y values of each K-step into the double-buffered y tiles and
-// signal each tile's full barrier; lane 0 of warp 12 waits for it, issues the K-step's 10 MMAs and
-// commits them to the buffer's done barrier, so the split never waits for MMA issue.  The split
+// signal each tile's full barrier; warp 12 waits for it, and one elected lane issues the K-step's
+// 10 MMAs and commits them to the buffer's done barrier, so the split never waits for MMA issue.  The split
 // warps also read the previous chunk's accumulators (and release them to the issuer through the
 // set's free barrier).  With 128 rows, row r sits in tensor-memory lane r: lanes 0-63 hold the top
 // halves and lanes 64-127 the bottom halves of the same 64 rows, so the warps of lane quarters
@@ -900,38 +928,39 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
     if (rec) {
         recurrence_warps<TA_YS>(A, m, blk, r, active, base, nch, cfirst, ybuf);
     } else if (issuer) {
-        // ------------------------------------------------ MMA issue (lane 0 of the last warp)
+        // ------------------------------------------------ MMA issue (one lane of the last warp)
         // per chunk q: wait until accumulator set q & 1 is read out (chunk q - 2), then per K-step
-        // until its y tile is written, issue its 10 MMAs and commit them to the buffer's done barrier
+        // until its y tile is written, issue its 10 MMAs and commit them to the buffer's done
+        // barrier.  The whole warp runs the loop (descriptors are base values plus constant
+        // offsets of the address field, kept warp-uniform); one elected lane issues.
         const uint32_t idesc = umma_idesc<TA_N>();  // M = 128, N = 64
+        const uint64_t dA0 = umma_desc(smem_u32(sX), TA_XKB, 128);
+        const uint64_t dB0 = umma_desc(smem_u32(sY), TA_BKB, 128);
+        const uint32_t issue = elect_one();
         for (int q = 0; q < nlive; ++q) {
             const int st = q & 1;
-            if (lane == 0 && q >= 2 && ok && !mbar_wait(&tfree[st], (uint32_t)(((q - 2) >> 1) & 1))) ok = false;
+            if (q >= 2 && ok && !mbar_wait(&tfree[st], (uint32_t)(((q - 2) >> 1) & 1))) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
 #pragma unroll 1
             for (int kk = 0; kk < TC_T / 16; ++kk) {
                 const int gk = 8 * q + kk, b = gk & 1;
-                if (lane == 0) {
-                    if (ok && !mbar_wait(&full[b], (uint32_t)((gk >> 1) & 1))) ok = false;
-                    if (ok) {
-                        asm volatile("tcgen05.fence::after_thread_sync;");
-                        const uint32_t a0 = smem_u32(sX) + (uint32_t)(kk * 2 * TA_XKB);
-                        const uint32_t b0 = smem_u32(sY + b * TA_BTILE);
-                        const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
+                if (ok && !mbar_wait(&full[b], (uint32_t)((gk >> 1) & 1))) ok = false;
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint64_t aK = dA0 + (uint64_t)((kk * 2 * TA_XKB) >> 4);  // address field: bytes / 16
+                const uint64_t bK = dB0 + (uint64_t)((b * TA_BTILE) >> 4);
 #pragma unroll
-                        for (int t = 0; t <= TC_MAXW; t += 2) {
+                for (int t = 0; t <= TC_MAXW; t += 2) {
 #pragma unroll
-                            for (int i = 0; i <= t; i += 2) {  // [X_i ; X_(i+1)] against [Y_(t-i) | Y_(t-i+1)]
-                                const int j = t - i;
-                                const uint64_t ad = umma_desc(a0 + i * (TA_R / 8) * 128, TA_XKB, 128);
-                                const uint64_t bd = umma_desc(b0 + j * TA_BDIG, TA_BKB, 128);
-                                umma_bf16(dt + (uint32_t)((t / 2) * TA_N), ad, bd, idesc,
-                                          (kk == 0 && i == 0) ? 0u : 1u);
-                            }
-                        }
-                        umma_commit(&mbar[b]);
+                    for (int i = 0; i <= t; i += 2) {  // [X_i ; X_(i+1)] against [Y_(t-i) | Y_(t-i+1)]
+                        const int j = t - i;
+                        umma_bf16_by(issue, dt + (uint32_t)((t / 2) * TA_N), aK + (uint64_t)((i * (TA_R / 8) * 128) >> 4),
+                                     bK + (uint64_t)((j * TA_BDIG) >> 4), idesc, (kk == 0 && i == 0) ? 0u : 1u);
                     }
                 }
-                __syncwarp();
+                umma_commit_by(issue, &mbar[b]);
             }
         }
         if (lane == 0 && !ok) atomicOr(A.status, 1);
