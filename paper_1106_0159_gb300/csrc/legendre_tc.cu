@@ -194,20 +194,6 @@ __device__ __forceinline__ uint32_t umma_idesc()
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-        smem_u32(mbar)));
-}
-
 // 1 in one lane of the (converged) warp, 0 in the others
 __device__ __forceinline__ uint32_t elect_one()
 {
@@ -563,34 +549,36 @@ __device__ __forceinline__ void recurrence_warps(const TcArgs &A, int m, int blk
     }
 }
 
-// Warp groups per CTA (one m, 128 slots, 384 threads):
+// Warp groups per CTA (one m, 128 slots, 416 threads):
 //   recurrence warps 0-3 (recurrence_warps): thread r runs the FP64 recurrence of slot r and
 //     writes each chunk's 32 values to a double-buffered y stage in shared memory;
 //   split warps 4-11: thread (par, r) cuts the 16 values of parity par of slot r into digits and
 //     stores row r of the parity's A tiles (double-buffered); all of them copy the chunk's a_lm
-//     digit tiles; lane 0 of warps 4-7 issues the MMAs of one (parity, class group) each and
-//     commits them to the stage's mbarrier; at the end they read tensor memory, warps 4-7 for
-//     the first half of the columns and warps 8-11 for the second.
+//     digit tiles and arrive on the stage's full mbarrier; at the end they read tensor memory,
+//     warps 4-7 for the first half of the columns and warps 8-11 for the second;
+//   warp 12: waits on the full mbarrier, and one elected lane issues the chunk's 2 x 28 MMAs
+//     (warp-uniform descriptors) and commits them to the stage's done mbarrier.
 // Stages: the y buffer is handed over with named barriers (FULL: recurrence arrives, split
 // waits; EMPTY: split arrives, recurrence waits, only where a later chunk reuses the stage);
-// the A/B tiles of a stage are rewritten after the mbarrier of the MMAs that read them.
+// the A/B tiles of a stage are rewritten after the done mbarrier of the MMAs that read them.
 template <int N>
-__global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
+__global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     using W = TcWs<N>;
     unsigned char *sA = smem;                               // [stage][parity][digit][128 x 16] bf16
     unsigned char *sB = smem + W::OFF_B;                    // [stage][parity][digit][N x 16] bf16
     double *ybuf = (double *)(smem + W::OFF_Y);             // [stage][32 l][128 slots]
-    uint64_t *mbar = (uint64_t *)(smem + W::OFF_BAR);       // [stage]
-    uint32_t *tslot = (uint32_t *)(mbar + 2);
+    uint64_t *mbar = (uint64_t *)(smem + W::OFF_BAR);       // done[stage]: the stage's MMAs complete
+    uint64_t *full = mbar + 2;                              // full[stage]: the stage's tiles written
+    uint32_t *tslot = (uint32_t *)(mbar + 4);
 
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
     if (m <= A.mR && A.s[blk * TC_T] < POLAR_SIN) return;  // Reinsch CTAs run in FP64
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool rec = warp < 4;
+    const bool rec = warp < 4, issuer = warp == TC_NT / 32;
     const int sp = tid - TC_T;                              // split-thread index 0..255
     const int r = rec ? tid : (sp & (TC_T - 1));            // slot within the block
     const int par = rec ? 0 : (sp >> 7);                    // split threads: parity of l - m they cut
@@ -603,7 +591,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
     const int nlive = nch - cfirst;
 
     if (nlive <= 0) {  // every value dropped: Delta_m is zero on these rings
-        if (!rec && par == 0 && active) {
+        if (!rec && !issuer && par == 0 && active) {
             const int rn = A.slotN[slot], rs = A.slotS[slot];
             const int64_t mstride = A.mmax + 1;
             for (int g = 0; g < A.nmaps; ++g) {
@@ -621,9 +609,10 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        // four issuing threads (parity x class group) commit to each stage's mbarrier
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(4));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(4));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[i])), "r"(1));         // commit
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(TC_NT - TC_T)); // split threads
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -634,9 +623,44 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
     bool ok = true;
     if (rec) {
         recurrence_warps<TC_T>(A, m, blk, r, active, base, nch, cfirst, ybuf);
-    } else {
-        // ------------------------------------------------ split / MMA group
+    } else if (issuer) {
+        // ------------------------------------------------ MMA issue (one lane of the last warp)
+        // per chunk: wait until the stage's tiles are written, issue its 2 x 28 MMAs (lane 0 of the
+        // split group's former issuers: parity eo, classes below NACC - 1 or the merged last class,
+        // each accumulator's MMAs in order) and commit them to the stage's done barrier.  The whole
+        // warp runs the loop with warp-uniform descriptors; one elected lane issues.
         const uint32_t idesc = umma_idesc<N>();
+        const uint64_t dA0 = umma_desc(smem_u32(sA), 16 * 128, 128);
+        const uint64_t dB0 = umma_desc(smem_u32(sB), (N / 8) * 128, 128);
+        const uint32_t issue = elect_one();
+        for (int q = 0; q < nlive; ++q) {
+            const int st = q & 1;
+            if (ok && !mbar_wait(&full[st], (uint32_t)((q >> 1) & 1))) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t aS = dA0 + (uint64_t)((st * W::A_BYTES) >> 4);  // address field: bytes / 16
+            const uint64_t bS = dB0 + (uint64_t)((st * W::B_CHUNK) >> 4);
+#pragma unroll
+            for (int eo = 0; eo < 2; ++eo) {
+#pragma unroll
+                for (int w = 0; w <= TC_MAXW; ++w) {
+#pragma unroll
+                    for (int i = 0; i <= w; ++i) {
+                        const int j = w - i;
+                        const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
+                        const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
+                        umma_bf16_by(issue, tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N),
+                                     aS + (uint64_t)(((eo * TC_S + i) * TC_ATILE) >> 4),
+                                     bS + (uint64_t)(((eo * TC_S + j) * TcTile<N>::B_TILE) >> 4), idesc, first ? 0u : 1u);
+                    }
+                }
+            }
+            umma_commit_by(issue, &mbar[st]);
+        }
+        if (lane == 0 && !ok) atomicOr(A.status, 1);
+    } else {
+        // ------------------------------------------------ split group
         const int64_t chunk0 = A.chunk_base[m];
         const int Ey = A.Ey[m * A.nblk + blk];
         constexpr int NS = TC_NT - TC_T;                 // split threads
@@ -680,31 +704,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_synth_kernel(TcArgs A)
             for (int i = 0; i < BV; ++i)
                 if (i * NS + sp < BTOT) ((uint4 *)b_st)[i * NS + sp] = breg[i];
             asm volatile("fence.proxy.async.shared::cta;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            ok = bar_red_and(BAR_SPLIT, NS, ok);
-            // lane 0 of warps 4-7 issues the MMAs of one (parity, class group): warp 4 + 2 eo the
-            // classes below NACC - 1 (10 MMAs), warp 5 + 2 eo the merged last class (18); each
-            // accumulator has one issuer, so its MMAs stay in order
-            if (ok && lane == 0 && sp < 128) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a0 = smem_u32(a_st), b0 = smem_u32(b_st);
-                const int eo = sp >> 6;
-                const bool last_group = ((sp >> 5) & 1) != 0;
-#pragma unroll
-                for (int w = 0; w <= TC_MAXW; ++w) {
-                    if ((w >= TcTile<N>::NACC - 1) != last_group) continue;
-#pragma unroll
-                    for (int i = 0; i <= w; ++i) {
-                        const int j = w - i;
-                        const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
-                        const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
-                        const uint64_t ad = umma_desc(a0 + (eo * TC_S + i) * TC_ATILE, 16 * 128, 128);
-                        const uint64_t bd = umma_desc(b0 + (eo * TC_S + j) * TcTile<N>::B_TILE, (N / 8) * 128, 128);
-                        umma_bf16(tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N), ad, bd, idesc, first ? 0u : 1u);
-                    }
-                }
-                umma_commit(&mbar[st]);
-            }
+            asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         }
         // the last commits cover every MMA issued: wait (bounded) before TMEM is read
         if (ok && !mbar_wait(&mbar[(nlive - 1) & 1], (uint32_t)(((nlive - 1) >> 1) & 1))) ok = false;
@@ -1116,7 +1116,7 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
     // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
     // and its accumulators take more than half of the tensor memory
     static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");
-    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT, TcWs<N>::SMEM, st>>>(A);
+    tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT + 32, TcWs<N>::SMEM, st>>>(A);
     return cudaGetLastError();
 }
 
