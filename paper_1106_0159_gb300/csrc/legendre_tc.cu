@@ -34,13 +34,14 @@
 // columns per parity need 10 N <= 320 of the 512 tensor-memory columns, so
 // one CTA runs per SM.
 //
-// Per CTA (one m, 128 slots, 256 threads in two warp groups), per chunk of 32 l:
+// Per CTA (one m, 128 slots, 416 threads in three warp groups), per chunk of 32 l:
 //   1. the recurrence warps run 32 steps of the two-instruction y recurrence (see
 //      legendre.cu), one slot per thread, and write the values to a y stage in shared memory;
 //   2. the split warps cut each value into digits with integer and FP32 operations, store
-//      them as the bf16 A tiles [parity][digit] of the chunk's stage, copy in the a_lm digit
-//      tiles (prepared by tc_split_b_kernel), and one thread issues the 2 x 28 MMAs (M = 128,
-//      N = 16 or 32, K = 16) and commits them to the stage's mbarrier.
+//      them as the bf16 A tiles [parity][digit] of the chunk's stage and copy in the a_lm digit
+//      tiles (prepared by tc_split_b_kernel);
+//   3. one lane of the issuing warp issues the 2 x 28 MMAs (M = 128, N = 16 or 32, K = 16) and
+//      commits them to the stage's mbarrier.
 // y values and tiles are double-buffered, so the FP64 recurrence of chunk c + 1 runs while
 // chunk c is split and multiplied: with one CTA per SM (tensor memory and shared memory
 // both allow one), a single warp group could not keep the FP64 pipe busy between its
@@ -625,10 +626,10 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
         recurrence_warps<TC_T>(A, m, blk, r, active, base, nch, cfirst, ybuf);
     } else if (issuer) {
         // ------------------------------------------------ MMA issue (one lane of the last warp)
-        // per chunk: wait until the stage's tiles are written, issue its 2 x 28 MMAs (lane 0 of the
-        // split group's former issuers: parity eo, classes below NACC - 1 or the merged last class,
-        // each accumulator's MMAs in order) and commit them to the stage's done barrier.  The whole
-        // warp runs the loop with warp-uniform descriptors; one elected lane issues.
+        // per chunk: wait until the stage's tiles are written, issue its 2 x 28 MMAs (per parity eo,
+        // classes 0 .. NACC - 2 alone and the rest merged, each accumulator's MMAs in order) and
+        // commit them to the stage's done barrier.  The whole warp runs the loop with warp-uniform
+        // descriptors; one elected lane issues.
         const uint32_t idesc = umma_idesc<N>();
         const uint64_t dA0 = umma_desc(smem_u32(sA), 16 * 128, 128);
         const uint64_t dB0 = umma_desc(smem_u32(sB), (N / 8) * 128, 128);
@@ -842,25 +843,28 @@ __device__ __forceinline__ float2 df_sum(float2 a, float2 b)
 
 // columns n0 .. n0 + 7 and 32 + n0 .. 32 + n0 + 7 (the two y-digit halves) of the 4 accumulator
 // regions of chunk buffer tb, this warp's lanes, summed as double-float pairs (classes roughly in
-// decreasing size)
+// decreasing size); the eight loads are issued together and waited for once
 __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int n0, float2 acc[8])
 {
+    uint32_t v[2 * TA_REG][8];
+#pragma unroll
+    for (int h = 0; h < 2 * TA_REG; ++h) {
+        const int reg = h >> 1, half = h & 1;
+        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) +
+                              (uint32_t)(tb * TA_ACC + reg * TA_N + half * TC_CH + n0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[h][0]), "=r"(v[h][1]), "=r"(v[h][2]), "=r"(v[h][3]), "=r"(v[h][4]), "=r"(v[h][5]),
+                       "=r"(v[h][6]), "=r"(v[h][7])
+                     : "r"(addr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int h = 0; h < 2 * TA_REG; ++h) {
-        const int reg = h >> 1, half = h & 1;
-        uint32_t v[8];
-        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) +
-                              (uint32_t)(tb * TA_ACC + reg * TA_N + half * TC_CH + n0);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                       "=r"(v[7])
-                     : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[t]));
+            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[h][t]));
             acc[t] = make_float2(sm.x, acc[t].y + sm.y);
         }
     }
@@ -872,7 +876,7 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
     unsigned char *sX = smem;                               // X digits (A operand), K-major
     unsigned char *sY = smem + TA_OFF_B;                    // [buffer] y digit tiles, K-major (B operand)
     double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
-    float2 *xch = (float2 *)(smem + TA_OFF_X);              // [64 rows][16 columns] bottom-half sums
+    float2 *xch = (float2 *)(smem + TA_OFF_X);              // [16 columns][64 rows] bottom-half sums
     int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
     uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // done[2] (MMAs of a B buffer complete),
     uint64_t *full = mbar + 2;                              // full[2] (a B buffer written),
@@ -1055,7 +1059,7 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[tb])) : "memory");
                 if (ok && qd >= 2) {
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) xch[erow * 16 + 8 * hf + t] = acc[t];
+                    for (int t = 0; t < 8; ++t) xch[(8 * hf + t) * TA_R + erow] = acc[t];
                 }
                 bar_sync(BAR_SPLIT, 2 * TC_T);  // bottom sums in xch
                 if (ok && qd < 2) {
@@ -1067,7 +1071,7 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                         const int l0 = m + TC_CH * (cfirst + qe);
 #pragma unroll
                         for (int t = 0; t < 8; ++t) {
-                            const float2 v = df_sum(acc[t], xch[erow * 16 + 8 * hf + t]);
+                            const float2 v = df_sum(acc[t], xch[(8 * hf + t) * TA_R + erow]);
                             const int l = l0 + 2 * ((n0 + t) & 15) + es;
                             if (l <= L) {
                                 float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
