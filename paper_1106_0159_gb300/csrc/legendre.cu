@@ -552,53 +552,6 @@ cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *de
     return cudaSuccess;
 }
 
-// The Reinsch-form CTAs only (slot block 0, m <= mR), for the precision form,
-// which leaves them to FP64.
-cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
-                                        int *nlaunch)
-{
-    *nlaunch = 0;
-    if (p.mR < 0 || !p.polar_first_slot) return cudaSuccess;
-    SynArgs A;
-    A.slotN = p.d_slotN;
-    A.slotS = p.d_slotS;
-    A.u = p.d_u;
-    A.s = p.d_s;
-    A.alpha = p.d_alpha;
-    A.cfac = p.d_cfac;
-    A.rein = p.d_rein;
-    A.mR = p.mR;
-    A.nslots = p.nslots;
-    A.nblk = 1;  // blockIdx.x = m, slot block 0
-    A.lmax = p.lmax;
-    A.mmax = p.mmax;
-    A.nrings = p.nrings;
-    A.nalm = p.nalm;
-    const unsigned grid = (unsigned)(p.mR + 1);
-    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
-    int g0 = 0;
-    while (g0 < nmaps) {
-        const int left = nmaps - g0;
-        A.alm = alm + (int64_t)g0 * p.nalm;
-        A.delta = delta + (int64_t)g0 * dstride;
-        const int most = p.tune[SHT_TUNE_SYNTH_MAPS];
-        if (left >= 4 && most >= 4) {
-            legendre_synth_kernel<4><<<grid, SYN_T, 0, st>>>(A);
-            g0 += 4;
-        } else if (left >= 2 && most >= 2) {
-            legendre_synth_kernel<2><<<grid, SYN_T, 0, st>>>(A);
-            g0 += 2;
-        } else {
-            legendre_synth_kernel<1><<<grid, SYN_T, 0, st>>>(A);
-            g0 += 1;
-        }
-        ++*nlaunch;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 size_t legendre_anal_partial_bytes(const Plan &p, int nmaps)
 {
     const int per = anal_slots_per_cta(p);

@@ -373,6 +373,112 @@ __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, cons
     }
 }
 
+// Polar slots of the precision-form synthesis (eq. DeltaDef): for m <= mR, slots 0 .. 127 (the
+// first block of the tensor-core synthesis), Reinsch's form of the recurrence in FP64 and the
+// sums E, O = sum over l of a_lm lambda_lm (l - m even, odd) in double-float on the FP32 pipe,
+// for up to NM maps per launch; Delta_N = E + O, Delta_S = E - O.  One CTA per m.
+constexpr int DFS_T = 128;  // threads = slots per CTA
+
+struct DfSynArgs {
+    const double2 *alm;    // [nmaps][nalm], first map of this launch
+    double2 *delta;        // [nmaps][nrings][mmax+1]
+    const int *slotN, *slotS;
+    const double *u, *s, *alpha;
+    const double3 *rein;   // Reinsch coefficients (beta_l, rho_l, b0_l) for m <= mR
+    int nslots, lmax, mmax, nrings, nmaps;
+    int64_t nalm;
+};
+
+template <int NM>
+__global__ void __launch_bounds__(DFS_T) synth_df_polar_kernel(DfSynArgs A)
+{
+    __shared__ double co[3][DF_CHL];     // beta_l, rho_l, b0_l of the chunk
+    __shared__ float4 sa[NM][DF_CHL];    // a_lm of the chunk as (re_hi, re_lo, im_hi, im_lo)
+    const int m = blockIdx.x;
+    const int tid = threadIdx.x;
+    const bool active = tid < A.nslots;
+    const int L = A.lmax;
+    const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
+
+    double u = 0.0, y1 = 0.0, y2 = 0.0;  // y1: lambda_(l-1), y2: D_(l-1)
+    int k = 0;
+    if (active) {
+        u = A.u[tid];
+        double y0;
+        sectoral_start(A.s[tid], A.alpha[base], m, y0, k);
+        y2 = y0;  // D_(m-1) = lambda_m with lambda_(m-1) = 0
+    }
+    float2 acc[2][NM][2];  // [E, O][map][re, im]
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int g = 0; g < NM; ++g) acc[p][g][0] = acc[p][g][1] = make_float2(0.f, 0.f);
+
+    for (int l0 = m; l0 <= L; l0 += DF_CHL) {
+        const int nl = min(DF_CHL, L - l0 + 1);
+        __syncthreads();
+        for (int i = tid; i < DF_CHL * (NM + 1); i += DFS_T) {
+            const int row = i / DF_CHL, j = i - row * DF_CHL;
+            const int64_t ix = base + (l0 - m) + j;
+            if (row == 0) {
+                const double3 c = (j < nl) ? A.rein[ix] : make_double3(0.0, 0.0, 0.0);
+                co[0][j] = c.x;
+                co[1][j] = c.y;
+                co[2][j] = c.z;
+            } else {
+                const int g = row - 1;
+                double2 a = make_double2(0.0, 0.0);
+                if (j < nl && g < A.nmaps) a = A.alm[(int64_t)g * A.nalm + ix];
+                const float2 re = d2df(a.x), im = d2df(m == 0 ? 0.0 : a.y);
+                sa[g][j] = make_float4(re.x, re.y, im.x, im.y);
+            }
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < nl; j0 += 16) {
+            const bool scaled = __any_sync(0xffffffffu, k < 0);
+            const int jn = min(j0 + 16, nl);
+            // steps in pairs: j even is l - m even (l0 - m is a multiple of 32), j + 1 odd
+            for (int j = j0; j < jn; j += 2) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    if (j + p < jn) {
+                        // D_l = (1 + rho_l) D_(l-1) + g_l lambda_(l-1), lambda_l = lambda_(l-1) + D_l
+                        const double gl = fma(-co[0][j + p], u, co[2][j + p]);
+                        const double t = fma(gl, y1, y2);
+                        y2 = fma(co[1][j + p], y2, t);
+                        y1 = y1 + y2;
+                        const float2 yd = (active && !(scaled && k < 0)) ? d2df(y1) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int g = 0; g < NM; ++g) {
+                            const float4 a = sa[g][j + p];
+                            acc[p][g][0] = df_add(acc[p][g][0], df_mul(yd, make_float2(a.x, a.y)));
+                            acc[p][g][1] = df_add(acc[p][g][1], df_mul(yd, make_float2(a.z, a.w)));
+                        }
+                    }
+                }
+            }
+            if (scaled && k < 0 && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
+                y1 *= 0x1p-512;
+                y2 *= 0x1p-512;
+                k += 1;
+            }
+        }
+    }
+    if (active) {
+        const int rn = A.slotN[tid], rs = A.slotS[tid];
+        const int64_t mstride = A.mmax + 1;
+#pragma unroll
+        for (int g = 0; g < NM; ++g) {
+            if (g >= A.nmaps) continue;
+            const double er = widen_df(acc[0][g][0]), ei = widen_df(acc[0][g][1]);
+            const double orr = widen_df(acc[1][g][0]), oi = widen_df(acc[1][g][1]);
+            double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+            if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
+            if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
+        }
+    }
+}
+
 template <int N, bool REIN>
 cudaError_t configure_df()
 {
@@ -425,6 +531,43 @@ cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar,
     reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, polar, polar_stride, polar_blocks, cfac, alm, nblk, nalm,
                                                    nmaps, lmax, blk_stride, map_stride, idx_stride, fp64_lim);
     return cudaGetLastError();
+}
+
+// The precision-form synthesis of the polar slots 0 .. 127 for m <= mR (nothing when the plan's
+// first ring is not polar), up to 8 maps per launch.
+cudaError_t launch_legendre_synth_df_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps,
+                                           cudaStream_t st, int *nlaunch)
+{
+    *nlaunch = 0;
+    if (p.mR < 0 || !p.polar_first_slot) return cudaSuccess;
+    DfSynArgs A{};
+    A.slotN = p.d_slotN;
+    A.slotS = p.d_slotS;
+    A.u = p.d_u;
+    A.s = p.d_s;
+    A.alpha = p.d_alpha;
+    A.rein = p.d_rein;
+    A.nslots = std::min(p.nslots, DFS_T);
+    A.lmax = p.lmax;
+    A.mmax = p.mmax;
+    A.nrings = p.nrings;
+    A.nalm = p.nalm;
+    const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
+    for (int g0 = 0; g0 < nmaps;) {
+        const int nm = std::min(8, nmaps - g0);
+        A.nmaps = nm;
+        A.alm = alm + (int64_t)g0 * p.nalm;
+        A.delta = delta + (int64_t)g0 * dstride;
+        if (nm > 4)
+            synth_df_polar_kernel<8><<<(unsigned)(p.mR + 1), DFS_T, 0, st>>>(A);
+        else
+            synth_df_polar_kernel<4><<<(unsigned)(p.mR + 1), DFS_T, 0, st>>>(A);
+        ++*nlaunch;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        g0 += nm;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t configure_df_kernels()

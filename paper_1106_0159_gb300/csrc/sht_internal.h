@@ -149,8 +149,9 @@ cudaError_t launch_legendre_anal_df_polar(const Plan &p, const double2 *delta, d
 cudaError_t build_tc_scales(Plan &p);
 cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 *delta, void *scratch, int nmaps,
                                      cudaStream_t st, int *nlaunch);
-cudaError_t launch_legendre_synth_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
-                                        int *nlaunch);
+// precision-form synthesis of the polar slots 0 .. 127 for m <= mR (Reinsch form, double-float sums)
+cudaError_t launch_legendre_synth_df_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps,
+                                           cudaStream_t st, int *nlaunch);
 
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st);

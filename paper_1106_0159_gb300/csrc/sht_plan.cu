@@ -267,7 +267,7 @@ sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, void 
     int n = 0;
     cudaError_t e;
     if (p.mode == SHT_MODE_SPLIT_BF16) {
-        e = sht::launch_legendre_synth_polar(p, alm, delta, nmaps, s, &n);
+        e = sht::launch_legendre_synth_df_polar(p, alm, delta, nmaps, s, &n);
         p.launches[0] += n;
         if (e == cudaSuccess) {
             e = sht::launch_legendre_synth_tc(p, alm, delta, tc_scratch, nmaps, s, &n);
