@@ -51,61 +51,13 @@
 namespace sht {
 namespace {
 
+#include "recurrence.cuh"
+
 constexpr int SYN_T = 128;      // threads (= ring slots) per synthesis CTA
 constexpr int ANA_T = 128;      // threads per analysis CTA
 constexpr int CHL = 128;        // l-values staged per shared-memory chunk (multiple of 16)
 constexpr int SUB = 16;         // steps between rescale tests
-constexpr int RESCALE_THR = 1023 + 256;  // biased exponent that triggers a rescale
 constexpr int RED_CL = 8;       // l-values per warp reduction round (analysis)
-constexpr double POLAR_SIN = 0.03;  // CTAs starting below this sin(theta) use the Reinsch form
-
-__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
-
-// v in [1, 2) times 2^e  <-  v (positive, normal)
-__device__ __forceinline__ void normalise(double &v, int &e)
-{
-    int hi = __double2hiint(v);
-    e += ((hi >> 20) & 0x7ff) - 1023;
-    hi = (hi & 0x800fffff) | (1023 << 20);
-    v = __hiloint2double(hi, __double2loint(v));
-}
-
-__device__ __forceinline__ double pow2i(int e)  // 2^e for -1022 <= e <= 1023
-{
-    return __hiloint2double((e + 1023) << 20, 0);
-}
-
-// lambda_mm = mu_m sin^m(theta) as y0 * 2^(512 k) with y0 <= mu_m
-__device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
-{
-    if (m > 0 && !(s > 1e-300)) {  // pole: lambda_lm = 0 for m > 0
-        y0 = 0.0;
-        k = 0;
-        return;
-    }
-    double r = 1.0;
-    int er = 0;
-    double b = s;
-    int eb = 0;
-    if (m > 0) normalise(b, eb);
-    for (int mm = m; mm; mm >>= 1) {
-        if (mm & 1) {
-            r *= b;
-            er += eb;
-            normalise(r, er);
-        }
-        if (mm > 1) {
-            b *= b;
-            eb *= 2;
-            normalise(b, eb);
-        }
-    }
-    // r * 2^er, r in [1, 2), er <= 0;  k = ceil(er / 512)
-    int kk = (er >= 0) ? 0 : -((-er) >> 9);
-    int rem = er - 512 * kk;  // in (-512, 0]
-    y0 = mu * r * pow2i(rem);
-    k = kk;
-}
 
 // Recurrence coefficients of one l-chunk in shared memory.
 struct Coef {

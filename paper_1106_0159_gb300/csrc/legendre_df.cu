@@ -42,50 +42,7 @@ static_assert(DF_G == 8 || DF_G == 16, "DF_G is 8 or 16");
 // Maps per launch: SHT_TUNE_DF_MAPS (16, 8 or 4; default 8).  Fewer maps: less shared memory and
 // more CTAs per SM, but the FP64 recurrence runs once per launch.  lmax = 4096, HEALPix 2048, 16 maps
 // on GB300: 16 maps per launch 809 ms, 8 maps 677 ms (two CTAs of 8 warps per SM), 4 maps 781 ms.
-constexpr int RESCALE_THR = 1023 + 256;
-constexpr double POLAR_SIN = 0.03;  // must match legendre.cu
-
-__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
-
-__device__ __forceinline__ void normalise(double &v, int &e)
-{
-    int hi = __double2hiint(v);
-    e += ((hi >> 20) & 0x7ff) - 1023;
-    hi = (hi & 0x800fffff) | (1023 << 20);
-    v = __hiloint2double(hi, __double2loint(v));
-}
-
-__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
-
-__device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
-{
-    if (m > 0 && !(s > 1e-300)) {
-        y0 = 0.0;
-        k = 0;
-        return;
-    }
-    double r = 1.0;
-    int er = 0;
-    double b = s;
-    int eb = 0;
-    if (m > 0) normalise(b, eb);
-    for (int mm = m; mm; mm >>= 1) {
-        if (mm & 1) {
-            r *= b;
-            er += eb;
-            normalise(r, er);
-        }
-        if (mm > 1) {
-            b *= b;
-            eb *= 2;
-            normalise(b, eb);
-        }
-    }
-    int kk = (er >= 0) ? 0 : -((-er) >> 9);
-    int rem = er - 512 * kk;
-    y0 = mu * r * pow2i(rem);
-    k = kk;
-}
+#include "recurrence.cuh"
 
 // v -> hi + lo from the bit pattern (integer pipe).  Values below 2^-126 flush to zero
 // (their share of any sum here is below 2^-100 of the largest term).

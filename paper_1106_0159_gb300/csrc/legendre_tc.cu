@@ -64,8 +64,6 @@ constexpr int TC_S = TC_DIGITS;     // digits per operand
 static_assert(TC_S >= 6 && TC_S <= 7, "the digit split needs 53 - (7 S - 1) >= 1 and class-0 sums below 2^24");
 constexpr int TC_CH = 32;           // l per chunk: 16 even + 16 odd
 constexpr int TC_ATILE = 128 * 16 * 2;  // bytes of one [128 x 16] bf16 tile
-constexpr int RESCALE_THR = 1023 + 256;
-constexpr double POLAR_SIN = 0.03;  // must match legendre.cu
 constexpr long long WAIT_POLLS = 1ll << 26;
 #ifndef TC_NACC
 #define TC_NACC 5       // accumulators per parity: classes 0 .. TC_NACC-2 alone, the rest together
@@ -74,52 +72,11 @@ constexpr long long WAIT_POLLS = 1ll << 26;
 #define TC_MAXW (TC_S - 1)  // highest digit class i + j accumulated
 #endif
 
-__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
-
-__device__ __forceinline__ void normalise(double &v, int &e)
-{
-    int hi = __double2hiint(v);
-    e += ((hi >> 20) & 0x7ff) - 1023;
-    hi = (hi & 0x800fffff) | (1023 << 20);
-    v = __hiloint2double(hi, __double2loint(v));
-}
-
-__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+#include "recurrence.cuh"
 
 __device__ __forceinline__ double pow2i_safe(int e)  // 2^e, 0 below the normal range
 {
     return e < -1022 ? 0.0 : pow2i(min(e, 1023));
-}
-
-// mu_m sin^m(theta) as y0 * 2^(512 k) (same construction as legendre.cu)
-__device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
-{
-    if (m > 0 && !(s > 1e-300)) {
-        y0 = 0.0;
-        k = 0;
-        return;
-    }
-    double r = 1.0;
-    int er = 0;
-    double b = s;
-    int eb = 0;
-    if (m > 0) normalise(b, eb);
-    for (int mm = m; mm; mm >>= 1) {
-        if (mm & 1) {
-            r *= b;
-            er += eb;
-            normalise(r, er);
-        }
-        if (mm > 1) {
-            b *= b;
-            eb *= 2;
-            normalise(b, eb);
-        }
-    }
-    int kk = (er >= 0) ? 0 : -((-er) >> 9);
-    int rem = er - 512 * kk;
-    y0 = mu * r * pow2i(rem);
-    k = kk;
 }
 
 // sum over the S digit positions of 64 * 128^s: added to a signed F in (-2^B, 2^B], it makes
