@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
+    ap.add_argument("--no-c2", dest="c2", action="store_false",
+                    help="skip the plain FP64 lmax = 2048 leg (HEALPix 1024 and the Gauss-Legendre round trip)")
     ap.add_argument("--prec-anal", default="tc", choices=["df", "tc"],
                     help="precision-form analysis kernel: tensor cores (default) or double-float")
     return ap.parse_args()
@@ -85,10 +87,9 @@ def mode_desc(a, mode=None):
     return MODES[mode] % ("tensor-core (split-bf16)" if a.prec_anal == "tc" else "double-float (FP32 pipe)")
 
 
-def workload_name(a, mode=None):
+def workload_name(a):
     return ("alm2map then map2alm round trip, HEALPix Nside=%d (%d px, %d rings), lmax=mmax=%d, "
-            "%d maps per step, %s" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps,
-                                       mode_desc(a, mode)))
+            "%d maps per step" % (a.nside, 12 * a.nside ** 2, 4 * a.nside - 1, a.lmax, a.maps))
 
 
 # ---------------------------------------------------------------- clocks during the timed region
@@ -152,8 +153,10 @@ class ClockSampler:
 
 def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0, alm=None, smap=None):
     """Time the oracle on `nrings_sample` rings of alm2map and `nm_sample` values of m of
-    map2alm; return (estimated seconds per map round trip, description, sample) where sample
-    holds the rings, the values of m and the oracle's outputs there (for accuracy checks)."""
+    map2alm (either may be 0); return (seconds per ring, seconds per m, description, sample)
+    where sample holds the rings, the values of m and the oracle's outputs there (for accuracy
+    checks).  The oracle's parallel loops run over the selected rings and values of m, so a
+    sample of at least as many items as host threads keeps every core busy."""
     import numpy as np
 
     import oracle
@@ -162,20 +165,42 @@ def oracle_sample(nside, lmax, nrings_sample, nm_sample, offset=0, alm=None, sma
 
     geom = geometry.healpix(nside)
     R = len(geom[0])
-    a = inputs.gaussian_alm(lmax, lmax, seed=100)[0] if alm is None else alm
-    rings = [int((offset + (k + 0.5) * R / nrings_sample)) % R for k in range(nrings_sample)]
-    t0 = time.perf_counter()
-    ring_vals = oracle.alm2map_rings(geom, a, lmax, lmax, rings)
-    t1 = time.perf_counter()
-    s = inputs.white_map(int(np.sum(geom[0])), seed=101)[0] if smap is None else smap
-    ms = [int((offset * 7 + (k + 0.5) * (lmax + 1) / nm_sample)) % (lmax + 1) for k in range(nm_sample)]
-    t2 = time.perf_counter()
-    alm_vals = oracle.map2alm_ms(geom, s, lmax, ms)
-    t3 = time.perf_counter()
-    est = (t1 - t0) * R / nrings_sample + (t3 - t2) * (lmax + 1) / nm_sample
-    desc = ("oracle alm2map on %d of %d rings (%.1f s) + map2alm on %d of %d values of m (%.1f s), "
-            "scaled to one full round trip" % (nrings_sample, R, t1 - t0, nm_sample, lmax + 1, t3 - t2))
-    return est, desc, {"rings": rings, "ring_vals": ring_vals, "ms": ms, "alm_vals": alm_vals}
+    rings = [int((offset + (k + 0.5) * R / max(nrings_sample, 1))) % R for k in range(nrings_sample)]
+    ms = [int((offset * 7 + (k + 0.5) * (lmax + 1) / max(nm_sample, 1))) % (lmax + 1) for k in range(nm_sample)]
+    ring_vals, alm_vals, tr, tm = None, None, 0.0, 0.0
+    if rings:
+        a = inputs.gaussian_alm(lmax, lmax, seed=100)[0] if alm is None else alm
+        t0 = time.perf_counter()
+        ring_vals = oracle.alm2map_rings(geom, a, lmax, lmax, rings)
+        tr = time.perf_counter() - t0
+    if ms:
+        s = inputs.white_map(int(np.sum(geom[0])), seed=101)[0] if smap is None else smap
+        t0 = time.perf_counter()
+        alm_vals = oracle.map2alm_ms(geom, s, lmax, ms)
+        tm = time.perf_counter() - t0
+    desc = ("oracle alm2map on %d of %d rings (%.1f s wall) + map2alm on %d of %d values of m (%.1f s wall)"
+            % (len(rings), R, tr, len(ms), lmax + 1, tm))
+    per_ring = tr / len(rings) if rings else None
+    per_m = tm / len(ms) if ms else None
+    return per_ring, per_m, desc, {"rings": rings, "ring_vals": ring_vals, "ms": ms, "alm_vals": alm_vals}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline lines."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def host_threads():
@@ -185,30 +210,58 @@ def host_threads():
         return os.cpu_count() or 1
 
 
+def workload_config(a):
+    """The `config` object both arms print: the workload, not the arm's arithmetic."""
+    return {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": a.lmax,
+            "mmax": a.lmax, "maps_per_step": a.maps, "directions": "alm2map then map2alm",
+            "accuracy": "<= 1e-9 of the RMS vs the oracle (precision form); <= 1e-11 (FP64)",
+            "l2": "inputs larger than L2 (a_lm %.2f GB, maps %.2f GB per step)"
+                  % (a.maps * (a.lmax + 1) * (a.lmax + 2) / 2 * 16 / 1e9, a.maps * 12 * a.nside ** 2 * 8 / 1e9)}
+
+
 def reference_arm(a, rank, world):
+    """The oracle on this host's cores.  Timed step k samples 16 rings of alm2map (k even) or 16
+    values of m of map2alm (k odd), rotating over the sphere; the value is one full round trip
+    per map extrapolated from the mean seconds per ring and per m over all timed steps (a
+    measured sample, scaled, not a full run).  Warm-up steps sample one value of m."""
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     nthr = host_threads()
-    per_step = []
-    desc = ""
-    for i in range(a.warmup + a.steps):
-        est, desc, _ = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, offset=i)
-        if i >= a.warmup:
-            per_step.append(est)
-    mean_s = statistics.mean(per_step)
-    value = 1.0 / mean_s
+    k_items = 16
+    for i in range(a.warmup):
+        oracle_sample(a.nside, a.lmax, 0, 1, offset=i)
+    ring_t, m_t, step_s = [], [], []
+    for i in range(a.steps):
+        t0 = time.perf_counter()
+        pr, pm, _, _ = oracle_sample(a.nside, a.lmax, k_items if i % 2 == 0 else 0, 0 if i % 2 == 0 else k_items,
+                                     offset=i)
+        step_s.append(time.perf_counter() - t0)
+        if pr is not None:
+            ring_t.append(pr)
+        if pm is not None:
+            m_t.append(pm)
+    if not m_t:  # a single timed step: sample m once more so that both halves are measured
+        m_t.append(oracle_sample(a.nside, a.lmax, 0, k_items, offset=a.steps)[1])
+    R = 4 * a.nside - 1
+    per_map_s = statistics.mean(ring_t) * R + statistics.mean(m_t) * (a.lmax + 1)
+    value = 1.0 / per_map_s
+    sample = ("extrapolated, not a full run: %d timed steps, each 16 rings of alm2map or 16 values of m of "
+              "map2alm (alternating, rotating offsets), %.2f s per ring and %.3f s per m (wall, %d threads), "
+              "scaled to %d rings + %d values of m = %.0f s per map round trip" %
+              (a.steps, statistics.mean(ring_t), statistics.mean(m_t), nthr, R, a.lmax + 1, per_map_s))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (long double oracle)", "data": DATA,
-        "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": a.lmax,
-                   "mmax": a.lmax, "maps_per_step": 1, "mode": "CPU oracle, bounded samples",
-                   "parallelism": "host threads"},
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(step_s) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "long double (80-bit x87 or binary128) CPU oracle", "data": DATA,
+        "config": workload_config(a),
         "cpu_baseline": {"value": value, "unit": "maps/s", "cores": nthr, "kind": "oracle",
-                         "sample": desc + " (last step)"},
+                         "cpu_model": cpu_model(), "extrapolated": True, "sample": sample},
         "e2e": {"value": value, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "ms_per_step is the measured wall time of one sample step; value is extrapolated to full "
+                "map round trips from the per-ring and per-m times",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -313,12 +366,20 @@ def ours_arm(a, rank, world, local_rank):
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe %.3f "
                                "TF/s" % (nsm, SM_MAX_MHZ, probe_tf),
                 "work": "7 flops per (l, m, ring-pair) step over the full triangle, per map (3 recurrence + 4 "
-                        "accumulate); steps whose lambda is below 2^-224 are skipped, so frac can exceed 1"}
+                        "accumulate); steps whose lambda is below 2^-224 are skipped, so frac can exceed 1",
+                "time": "the Legendre stage (all its launches)",
+                "live_share": live_share, "frac_of_executed": achieved / peak_tf * live_share}
+
+    # live share of the (l, m, ring-pair) steps: the precision-form tables mark the first 32-l chunk
+    # per (m, 128-slot block) above the dropping threshold; the plain kernels skip the same prefix
+    # per warp, so the nominal fractions below count about 1 / live more work than is executed
+    plan.set_mode(sht.MODE_SPLIT_BF16)
+    live_steps, total_steps = plan.live_steps()
+    live_share = live_steps / total_steps
 
     def split_roofline(run, steps):
         st = run["stages"]
-        anal = st["legendre_anal"][0] >= st["legendre_synth"][0]
-        if anal and plan.tuning(sht.TUNE_PREC_ANAL) == 0:
+        if plan.tuning(sht.TUNE_PREC_ANAL) == 0 and st["legendre_anal"][0] >= st["legendre_synth"][0]:
             # double-float analysis on the FP32 pipe: per (l, m, ring-pair, map) two real products
             # (1 FMUL + 3 FFMA = 7 flops each) and their double-float sums (TwoSum + 2 adds = 8 flops)
             ms = st["legendre_anal"][0]
@@ -328,28 +389,45 @@ def ours_arm(a, rank, world, local_rank):
                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": traffic_from_profiles("legendre_anal_df_kernel"),
                     "peak_source": "derived: 128 FP32 FMA/clk/SM x %d SMs x %d MHz x 2 flop" % (nsm, SM_MAX_MHZ),
-                    "work": "30 FP32 flops per (l, m, ring-pair, map): two double-float real products and sums"}
-        # tensor-core kernels: bound by their FP64 recurrence (2 DFMA per (l, m, ring-pair) step,
-        # once per launch of up to 16 maps); the contraction's useful tensor work is 28 digit
-        # products x 2 flops per step and real column (2 per map).  The stage time includes the
-        # polar-block FP64 kernels (and the block reduction of the analysis), so this is a lower
-        # bound on the kernel's own rate
-        ms = st["legendre_anal"][0] if anal else st["legendre_synth"][0]
-        per = 16
-        launches = -(-B // per)
-        achieved = 4.0 * S * launches * steps / (ms * 1e-3) / 1e12
-        tensor = 56.0 * S * 2 * B * steps / (ms * 1e-3) / 1e12
-        tpeak = MEASURED.get("bf16_tflops_sustained") or 1725.1
+                    "work": "30 FP32 flops per (l, m, ring-pair, map): two double-float real products and sums",
+                    "time": "analysis stage (includes the polar kernel and the block reduction)"}
+        # the tensor-core kernels, each timed alone by its own CUDA events on the call's stream
+        # (stage ids tc_synth_kernel / tc_anal_kernel: no polar kernel, no block reduction)
+        ka_ms, ka_n = st["tc_anal_kernel"]
+        ks_ms, ks_n = st["tc_synth_kernel"]
+        anal = ka_ms >= ks_ms
+        ms, nl = (ka_ms, ka_n) if anal else (ks_ms, ks_n)
         key = "tc_anal_kernel" if anal else "tc_synth_kernel"
-        return {"bound": "alu", "pipe": "fp64 (recurrence)", "kernel": key, "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic_from_profiles(key),
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe %.3f "
-                               "TF/s" % (nsm, SM_MAX_MHZ, probe_tf),
-                "work": "4 FP64 flops per (l, m, ring-pair) step over the full triangle, once per launch "
-                        "(%d maps per launch)" % per,
-                "tensor": {"achieved": tensor, "peak": tpeak, "unit": "TFLOP/s", "frac": tensor / tpeak,
-                           "work": "28 bf16 digit products x 2 flops per (l, m, ring-pair) step and real column",
-                           "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json)"}}
+        per_launch_s = ms * 1e-3 / nl
+        maps_per_launch = min(B, 16)
+        # binding pipe: the tensor cores.  Useful work = the 28 digit-pair slice-products, each the
+        # whole contraction of 4 flops per (l, m, ring-pair) step and map (complex x real), over the
+        # full triangle S
+        tflops = 28 * 4.0 * maps_per_launch * S / per_launch_s / 1e12
+        tpeak = MEASURED.get("bf16_tflops_sustained") or 1725.1
+        # the FP64 recurrence beside it: 3 flops per step, once per launch
+        fflops = 3.0 * S / per_launch_s / 1e12
+        # algorithmic bytes per launch: Delta read and a_lm written (analysis), a_lm read and
+        # Delta written (synthesis)
+        alg = maps_per_launch * (plan.nrings * (L + 1) + nalm) * 16
+        traffic = traffic_from_profiles(key)
+        return {"bound": "tensor", "kernel": key, "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": tflops / tpeak, "traffic": traffic,
+                "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained): the "
+                               "kernel is timed inside a long step",
+                "work": "28 bf16 digit-pair products x 4 flops per (l, m, ring-pair) step and map, nominal full "
+                        "triangle S = %d steps, %d maps per launch: %.3e flops per launch" %
+                        (S, maps_per_launch, 28 * 4.0 * maps_per_launch * S),
+                "time": "the kernel's own launches (CUDA events around each launch on the call's stream): "
+                        "%.2f ms per launch, %d launches" % (per_launch_s * 1e3, nl),
+                "live_share": live_share,
+                "frac_of_executed": tflops / tpeak / live_share,
+                "fp64": {"achieved": fflops, "peak": peak_tf, "unit": "TFLOP/s", "frac": fflops / peak_tf,
+                         "work": "3 FP64 flops per (l, m, ring-pair) step of the recurrence, once per launch",
+                         "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %d MHz x 2 flop; in-run FMA probe "
+                                        "%.3f TF/s" % (nsm, SM_MAX_MHZ, probe_tf)},
+                "algorithmic_bytes": alg,
+                "traffic_over_algorithmic": (traffic / alg) if traffic else None}
 
     head = timed(a.mode, a.steps, a.warmup, True)
     total_ms, step_ms, stages, clk = head["total_ms"], head["step_ms"], head["stages"], head["clocks"]
@@ -452,8 +530,14 @@ def ours_arm(a, rank, world, local_rank):
         nthr = host_threads()
         a0 = host_alm[0].numpy()
         s0 = mp[0].cpu().numpy() if accuracy else None
-        est, desc, smp = oracle_sample(a.nside, a.lmax, max(4, min(nthr, 16)), 1, alm=a0, smap=s0)
-        cpu = {"value": 1.0 / est, "unit": "maps/s", "cores": nthr, "kind": "oracle", "sample": desc}
+        k_items = 16
+        pr, pm, desc, smp = oracle_sample(a.nside, a.lmax, k_items, k_items, alm=a0, smap=s0)
+        per_map_s = pr * plan.nrings + pm * (L + 1)
+        cpu = {"value": 1.0 / per_map_s, "unit": "maps/s", "cores": nthr, "kind": "oracle",
+               "cpu_model": cpu_model(), "extrapolated": True,
+               "sample": "extrapolated, not a full run: " + desc + ", %.2f s per ring and %.3f s per m, scaled to "
+                         "%d rings + %d values of m = %.0f s per map round trip" %
+                         (pr, pm, plan.nrings, L + 1, per_map_s)}
         if accuracy:
             # the same oracle outputs checked against map 0 of the batch (rings and m of the sample)
             ofs = np.concatenate([[0], np.cumsum(np.asarray(geom[0], dtype=np.int64))])
@@ -484,13 +568,9 @@ def ours_arm(a, rank, world, local_rank):
                       + ("bf16 digits (tcgen05)" if a.prec_anal == "tc" else "double-float (f32 pairs)"))
                      if a.mode == "split" else "f64",
             "data": DATA,
-            "config": {"workload": workload_name(a), "grid": "HEALPix", "nside": a.nside, "lmax": L, "mmax": L,
-                       "maps_per_step": B, "mode": mode_desc(a),
-                       "accuracy": "<= 1e-9 of the RMS vs the oracle" if a.mode == "split" else "<= 1e-11 of the RMS",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (a_lm %.2f GB, maps %.2f GB per step)"
-                             % (B * nalm * 16 / 1e9, B * npix * 8 / 1e9),
-                       "plan_create_s": plan_s},
+            "config": workload_config(a),
+            "mode": mode_desc(a), "parallelism": "replicas" if world > 1 else "single GPU",
+            "plan_create_s": plan_s,
             "latency_ms": {"p50": statistics.median(q), "p99": q[min(len(q) - 1, int(0.99 * len(q)))],
                            "per": "step (%d-map round trip)" % B},
             "roofline": roofline,
@@ -510,12 +590,120 @@ def ours_arm(a, rank, world, local_rank):
     torch.cuda.empty_cache()
     serve_res = serve_leg(a, rep, local_rank) if a.serve_requests > 0 else None
     batch_res = batch_leg(a, rep, local_rank) if a.batch_maps > 0 else None
+    c2_res = c2_leg(a, rep, local_rank, nsm, peak_tf) if a.c2 else None
     if rank == 0:
         line["serve"] = serve_res
         line["batched"] = batch_res
+        line["c2_plain_fp64_lmax2048"] = c2_res
+        if cpu is not None:
+            cpu["o1_c1"] = o1_leg()
         print(json.dumps(line), flush=True)
     rep.close()
     return 0
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)  # a write larger than L2 between timed repetitions
+
+
+def c2_leg(a, rep, local_rank, nsm, peak_tf):
+    """Plain FP64 at lmax = mmax = 2048, one map per call: alm2map and map2alm on HEALPix Nside
+    1024 (12.6 M pixels), each timed alone, and the Gauss-Legendre 2049 x 4097 round trip with
+    its error (the quadrature is exact there, so map2alm(alm2map(a)) = a).  Each repetition is
+    timed with its own CUDA events after an L2 flush (the inputs fit in L2 at this size)."""
+    import numpy as np
+    import torch
+
+    from paper_1106_0159_gb300 import inputs, sht
+
+    L, reps = 2048, 3
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            _flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    out = {}
+    for name, geom, grid, inp in (("healpix1024", sht.healpix_geometry(1024), sht.GRID_HEALPIX, "gaussian"),
+                                  ("gl2049x4097", sht.gauss_legendre_geometry(2049, 4097),
+                                   sht.GRID_GAUSS_LEGENDRE, "uniform")):
+        plan = sht.Plan(geom, L, L, grid=grid)
+        if inp == "gaussian":
+            ah = inputs.gaussian_alm(L, L, seed=rep.seed(2048), nmaps=1)
+        else:
+            ah = inputs.uniform_alm(L, L, seed=rep.seed(2049), nmaps=1)
+        alm = torch.from_numpy(ah).cuda()
+        mp = torch.empty((1, plan.npix), dtype=torch.float64, device="cuda")
+        back = torch.empty((1, plan.nalm), dtype=torch.complex128, device="cuda")
+        plan.alm2map(alm, out=mp)
+        plan.set_stage_timing(True)
+        plan.stage_times(reset=True)
+        t_syn = timed(lambda: plan.alm2map(alm, out=mp))
+        st_syn = plan.stage_times(reset=True)
+        t_ana = timed(lambda: plan.map2alm(mp, out=back))
+        st_ana = plan.stage_times(reset=True)
+        plan.set_stage_timing(False)
+        S = sum(L - m + 1 for m in range(L + 1)) * plan.npairs
+        n = reps + 1
+
+        def roof(ms_total):
+            ach = 7.0 * S / (ms_total / n * 1e-3) / 1e12
+            return {"achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf}
+
+        r = {"npix": plan.npix, "nrings": plan.nrings, "alm2map_ms": t_syn, "map2alm_ms": t_ana,
+             "round_trip_maps_per_s": 1e3 / (t_syn + t_ana),
+             "stages_ms": {"alm2map": {k: v[0] / n for k, v in st_syn.items() if v[1]},
+                           "map2alm": {k: v[0] / n for k, v in st_ana.items() if v[1]}},
+             "fp64_roofline": {"legendre_synth": roof(st_syn["legendre_synth"][0]),
+                               "legendre_anal": roof(st_ana["legendre_anal"][0]),
+                               "work": "7 flops per (l, m, ring-pair) step, nominal full triangle S = %d" % S},
+             "input": inp}
+        if grid == sht.GRID_GAUSS_LEGENDRE:
+            d = (back - alm).abs().max().item() / alm.abs().pow(2).mean().sqrt().item()
+            r["round_trip_err"] = {"max_abs_over_rms": d, "bar": 1e-12,
+                                   "input": "uniform a_lm in (-1, 1) (the paper's accuracy input)"}
+        out[name] = r
+        del alm, mp, back
+        plan.close()
+    del flush
+    torch.cuda.empty_cache()
+    out["form"] = "plain FP64, 1 map per call, lmax = mmax = 2048, median of %d repetitions after an L2 flush" % reps
+    return out
+
+
+def o1_leg(lmax=64, nside=32):
+    """The oracle's exact pixel-by-pixel form (eqs. alm2mapDef / map2almDef with lambda recomputed
+    per pixel), single-threaded, at HEALPix Nside 32, lmax 64, one map: seconds per transform."""
+    import oracle
+    from oracle import geometry
+    from paper_1106_0159_gb300 import inputs
+
+    oracle.build()
+    geom = geometry.healpix(nside)
+    a0 = inputs.gaussian_alm(lmax, lmax, seed=7)[0]
+    old = oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        s0 = oracle.alm2map_exact(geom, a0, lmax, lmax)
+        t1 = time.perf_counter()
+        oracle.map2alm_exact(geom, s0, lmax, lmax)
+        t2 = time.perf_counter()
+    finally:
+        oracle.set_threads(old)
+    return {"alm2map_s": t1 - t0, "map2alm_s": t2 - t1, "round_trip_maps_per_s": 1.0 / (t2 - t0), "cores": 1,
+            "cpu_model": cpu_model(), "form": "oracle O1 (pixel by pixel), one thread, HEALPix Nside %d, lmax %d, "
+                                            "1 map" % (nside, lmax)}
 
 
 def batch_leg(a, rep, local_rank):

@@ -87,7 +87,10 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings,
  *                        FP64 or double-float.  The ring DFTs run in double-float on the FP32 pipe.
  *                        SHT_TUNE_PREC_ANAL and SHT_TUNE_PREC_RING select other kernels.  Relative
  *                        error against the exact transform <= 1e-9 of the output RMS.  Processes up
- *                        to 16 maps per pass over the recurrence.
+ *                        to 16 maps per pass over the recurrence.  Only the first 128 ring slots
+ *                        (after north/south pairing, ordered from the poles) may lie within
+ *                        sin(theta) < 0.03 of a pole; a grid with more polar slots (HEALPix
+ *                        Nside >~ 3500) returns SHT_EUNSUPPORTED and stays in its old mode.
  * Switching to SHT_MODE_SPLIT_BF16 the first time runs one FP64 pass of the recurrence to
  * measure the scale of its values per (m, block of 128 ring slots) (synchronous; about the cost
  * of one single-map synthesis).  SHT_EINVAL for an unknown mode.
@@ -98,11 +101,23 @@ int        sht_plan_mode(sht_plan_t plan);
 
 /*
  * Device status word of the plan: bit 0 is set when a bounded wait inside a tensor-core kernel
- * gave up (the kernel then wrote no output for that block and released its resources).
- * Copies the word to *status (synchronous, after the device finishes its work); clear != 0 resets
- * it.  Returns SHT_ETIMEOUT while bit 0 is set (read before the clear), SHT_OK otherwise.
+ * gave up.  That kernel then skipped its output and released its resources, but MMAs it had
+ * already issued may still have run, so treat the whole output of every call since the last
+ * clear as untrusted, not only the block that timed out.  Waits for all work on the device
+ * (cudaDeviceSynchronize, so kernels on non-blocking streams are finished too), then copies the
+ * word to *status; clear != 0 resets it (and waits for the reset).  Returns SHT_ETIMEOUT while
+ * bit 0 is set (read before the clear), SHT_OK otherwise.
  */
 sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear);
+
+/*
+ * Work accounting (host call, synchronous): the (l, m, ring-slot) recurrence steps of one pass,
+ * *total = nalm * slots, and *live, those from the first 32-l chunk of each (m, block of 128
+ * slots) in which some lambda is above the 2^-256 dropping threshold of the rescaling scheme
+ * (steps before it contribute exactly zero and the precision-form kernels skip their sums).
+ * Needs the tables made by the first switch to SHT_MODE_SPLIT_BF16; SHT_EINVAL before that.
+ */
+sht_status sht_plan_live_steps(sht_plan_t plan, int64_t *live, int64_t *total);
 
 /*
  * Failure-path self test (no counterpart in the paper): enqueues on `stream` a one-block kernel
@@ -208,12 +223,25 @@ sht_status sht_geom_gauss_legendre(int nrings, int64_t nphi, int64_t *nphi_out, 
 /*
  * Per-stage accounting.  Kernel launches are always counted; with timing
  * enabled, every stage of every transform call is bracketed by CUDA events
- * recorded on the call's stream.  Stage ids: 0 Legendre synthesis,
- * 1 ring synthesis, 2 ring analysis, 3 Legendre analysis, 4 ring-block
- * reduction of the analysis.  sht_plan_stage_times waits for the recorded
- * events, adds their durations to the running totals, and writes the totals
- * (ms[5], launches[5]); reset != 0 zeroes the totals afterwards.
+ * recorded on the call's stream.  Stage ids (SHT_NSTAGES of them): 0 Legendre
+ * synthesis, 1 ring synthesis, 2 ring analysis, 3 Legendre analysis, 4 ring-block
+ * reduction of the FP64 analysis; 5 and 6 time one kernel alone, the main
+ * tensor-core kernel of the precision-form synthesis (inside stage 0) and of the
+ * precision-form analysis (inside stage 3), so that a roofline can divide by that
+ * kernel's own time.  sht_plan_stage_times waits for the recorded events, adds
+ * their durations to the running totals, and writes the totals
+ * (ms[SHT_NSTAGES], launches[SHT_NSTAGES]); reset != 0 zeroes the totals afterwards.
  */
+enum {
+    SHT_STAGE_LEGENDRE_SYNTH = 0,
+    SHT_STAGE_RING_SYNTH = 1,
+    SHT_STAGE_RING_ANAL = 2,
+    SHT_STAGE_LEGENDRE_ANAL = 3,
+    SHT_STAGE_BLOCK_REDUCE = 4,
+    SHT_STAGE_TC_SYNTH_KERNEL = 5,
+    SHT_STAGE_TC_ANAL_KERNEL = 6,
+    SHT_NSTAGES = 7
+};
 sht_status sht_plan_set_stage_timing(sht_plan_t plan, int enable);
 sht_status sht_plan_stage_times(sht_plan_t plan, double *ms, int64_t *launches, int reset);
 
@@ -226,14 +254,17 @@ sht_status sht_fp64_fma_tflops(double *tflops);
 
 /*
  * Synthesis for callers that cannot allocate device memory (the paper has no
- * counterpart; this is a library service).  Same arguments, layouts and
- * stream ordering as sht_alm2map, but the call allocates nothing: its
- * scratch (the Delta intermediate plus the ring-FFT buffers) is a 64 MiB
- * static device array, sht_noalloc_scratch_bytes(), that every GPU loading
- * this library holds until the process exits.  Calls whose scratch
- * (16 nmaps nrings (mmax+1) bytes, rounded up to 256, plus one ring-FFT
- * buffer of 48 * max ring length bytes) exceeds it return SHT_EINVAL with
- * the sizes in sht_plan_last_error.  The first call on a device looks up the
+ * counterpart; this is a library service).  Same arguments, layouts, stream
+ * ordering and arithmetic as sht_alm2map (the plan's mode: the FP64 path, or
+ * the precision form's kernels on a SHT_MODE_SPLIT_BF16 plan), but the call
+ * allocates nothing: its scratch (the Delta intermediate, then either the
+ * precision form's digit tiles or the ring-FFT buffers) is a 64 MiB static
+ * device array, sht_noalloc_scratch_bytes(), that every GPU loading this
+ * library holds until the process exits.  Calls whose scratch
+ * (16 nmaps nrings (mmax+1) bytes, rounded up to 256, plus the larger of one
+ * ring-FFT buffer of 48 * max ring length bytes and, in the precision form,
+ * the digit tiles of c_lm a_lm) exceeds it return SHT_EINVAL with the sizes
+ * in sht_plan_last_error.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and caches it: make that
  * first call before any stream capture.  All calls share the one array, so
  * calls that overlap on the GPU (other streams, other threads, other plans)

@@ -66,6 +66,8 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = None
+        lib.oracle_set_threads.argtypes = [I]
+        lib.oracle_set_threads.restype = I
         lib.oracle_log_mu.argtypes = [I]
         lib.oracle_log_mu.restype = D
         _lib = lib
@@ -98,6 +100,12 @@ def nalm(lmax: int, mmax: int) -> int:
 
 def alm_index(lmax: int, l: int, m: int) -> int:
     return m * (2 * lmax + 3 - m) // 2 + (l - m)
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's parallel loops from now on (timing only; results do not
+    depend on it).  Returns the previous count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def lambda_lm(theta: float, lmax: int, m: int) -> np.ndarray:

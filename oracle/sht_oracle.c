@@ -37,6 +37,7 @@
  *   - Im a_{l0} is ignored on input (real map).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -377,4 +378,14 @@ void oracle_legendre_anal(int nrings, const double *theta, int lmax, int nm, con
         o += n;
         free(part);
     }
+}
+
+/* Host threads the oracle's parallel loops use from now on (timing only: every result is the
+ * same for any count, since each output value is summed by one thread in a fixed order).
+ * Returns the previous count. */
+int oracle_set_threads(int n)
+{
+    const int old = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return old;
 }

@@ -1077,7 +1077,10 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
     // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
     // and its accumulators take more than half of the tensor memory
     static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");
+    StageEvents ev(p, SHT_STAGE_TC_SYNTH_KERNEL, st);
     tc_synth_kernel<N><<<(unsigned)((p.mmax + 1) * A.nblk), TC_NT + 32, TcWs<N>::SMEM, st>>>(A);
+    p.launches[SHT_STAGE_TC_SYNTH_KERNEL] += 1;
+    ev.done();
     return cudaGetLastError();
 }
 
@@ -1145,7 +1148,12 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
         A.nmaps = nm;
         A.delta = const_cast<double2 *>(delta) + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial;
-        tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TA_NT, TA_SMEM, st>>>(A);
+        {
+            StageEvents ev(p, SHT_STAGE_TC_ANAL_KERNEL, st);
+            tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TA_NT, TA_SMEM, st>>>(A);
+            p.launches[SHT_STAGE_TC_ANAL_KERNEL] += 1;
+            ev.done();
+        }
         ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -26,7 +26,7 @@ __device__ __forceinline__ double pow2i(int e)  // 2^e for -1022 <= e <= 1023
     return __hiloint2double((e + 1023) << 20, 0);
 }
 
-// lambda_mm = mu_m sin^m(theta) as y0 * 2^(512 k), k <= 0, y0 <= mu_m (binary powering of
+// lambda_mm = mu_m sin^m(theta) as y0 * 2^(512 k), k <= 0, y0 < 2 mu_m (binary powering of
 // sin(theta) with the exponent kept in an int); 0 at the pole for m > 0
 __device__ void sectoral_start(double s, double mu, int m, double &y0, int &k)
 {

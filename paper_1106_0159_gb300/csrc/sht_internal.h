@@ -88,19 +88,32 @@ struct Plan {
     void *d_ws = nullptr;
     size_t ws_bytes = 0;
 
-    // per-stage accounting: launches always, device time when enabled
-    enum { NSTAGE = 5 };
+    // per-stage accounting: launches always, device time when enabled (stage ids as in sht.h;
+    // the kernel-only stages are recorded by the launchers, which see a const plan)
+    enum { NSTAGE = SHT_NSTAGES };
     bool timing = false;
-    int64_t launches[NSTAGE] = {0, 0, 0, 0, 0};
-    double stage_ms[NSTAGE] = {0, 0, 0, 0, 0};
+    mutable int64_t launches[NSTAGE] = {};
+    double stage_ms[NSTAGE] = {};
     struct Pending {
         int stage;
         cudaEvent_t a, b;
     };
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> event_pool;
+    mutable std::vector<Pending> pending;
+    mutable std::vector<cudaEvent_t> event_pool;
 
     std::string last_error;
+};
+
+// CUDA events recorded on the call's stream around a stage or one kernel launch while the plan's
+// stage timing is on (sht_plan_set_stage_timing); done() queues the pair for sht_plan_stage_times.
+struct StageEvents {
+    const Plan &p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageEvents(const Plan &pl, int st, cudaStream_t str);
+    void done();
+    ~StageEvents();
 };
 
 // launch helpers (legendre.cu, ringfft.cu); return cudaGetLastError(), count launches in *nlaunch

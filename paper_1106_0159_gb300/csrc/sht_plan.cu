@@ -9,6 +9,49 @@
 #include <new>
 #include <numeric>
 
+namespace sht {
+
+static cudaEvent_t pool_event(const Plan &p)
+{
+    if (!p.event_pool.empty()) {
+        cudaEvent_t e = p.event_pool.back();
+        p.event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+StageEvents::StageEvents(const Plan &pl, int st, cudaStream_t str) : p(pl), stage(st), s(str)
+{
+    if (p.timing) {
+        a = pool_event(p);
+        b = pool_event(p);
+        if (a && b) cudaEventRecord(a, s);
+    }
+}
+
+void StageEvents::done()
+{
+    if (a && b) {
+        cudaEventRecord(b, s);
+        p.pending.push_back({stage, a, b});
+        a = b = nullptr;
+    }
+}
+
+StageEvents::~StageEvents()
+{
+    if (a) p.event_pool.push_back(a);
+    if (b) p.event_pool.push_back(b);
+}
+
+}  // namespace sht
+
 using sht::Plan;
 
 namespace {
@@ -216,48 +259,8 @@ sht_status check_call(sht_plan_t plan, const void *in, const void *out, int nmap
 
 
 // --- stage runners: launches plus optional event bracketing on the call's stream
-cudaEvent_t pool_event(Plan &p)
-{
-    if (!p.event_pool.empty()) {
-        cudaEvent_t e = p.event_pool.back();
-        p.event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return e;
-}
-
-struct StageScope {
-    Plan &p;
-    int stage;
-    cudaStream_t s;
-    cudaEvent_t a = nullptr, b = nullptr;
-    StageScope(Plan &pl, int st, cudaStream_t str) : p(pl), stage(st), s(str)
-    {
-        if (p.timing) {
-            a = pool_event(p);
-            b = pool_event(p);
-            if (a && b) cudaEventRecord(a, s);
-        }
-    }
-    void done()
-    {
-        if (a && b) {
-            cudaEventRecord(b, s);
-            p.pending.push_back({stage, a, b});
-            a = b = nullptr;
-        }
-    }
-    ~StageScope()
-    {
-        if (a) p.event_pool.push_back(a);
-        if (b) p.event_pool.push_back(b);
-    }
-};
+using sht::StageEvents;
+using StageScope = StageEvents;
 
 // tc_scratch: tc_workspace_bytes(p, min(nmaps, 16)) bytes, used in the precision form only
 sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, void *tc_scratch, int nmaps,
@@ -443,10 +446,36 @@ sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
 {
     if (!plan || !status) return SHT_EINVAL;
     Plan &p = plan->p;
-    cudaError_t e = cudaMemcpy(status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    // kernels on non-blocking streams do not order against the legacy stream of cudaMemcpy:
+    // wait for the whole device first, so that no kernel can set the bit after the read
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && clear) e = cudaMemset(p.d_status, 0, sizeof(int));
+    if (e == cudaSuccess && clear) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(p, e, "device status");
     return (*status & 1) ? SHT_ETIMEOUT : SHT_OK;
+}
+
+sht_status sht_plan_live_steps(sht_plan_t plan, int64_t *live, int64_t *total)
+{
+    if (!plan || !live || !total) return SHT_EINVAL;
+    Plan &p = plan->p;
+    if (!p.d_tc_Ey) return SHT_EINVAL;  // the tables come with the first switch to the precision form
+    const int nblk = (p.nslots + 127) / 128;
+    std::vector<int> first((size_t)(p.mmax + 1) * nblk);
+    cudaError_t e = cudaMemcpy(first.data(), p.d_tc_Ey + first.size(), sizeof(int) * first.size(),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "live steps");
+    int64_t lv = 0;
+    for (int m = 0; m <= p.mmax; ++m)
+        for (int b = 0; b < nblk; ++b) {
+            const int64_t nl = (int64_t)(p.lmax - m + 1) - 32 * (int64_t)first[(size_t)m * nblk + b];
+            const int64_t ns = std::min(128, p.nslots - 128 * b);
+            if (nl > 0) lv += nl * ns;
+        }
+    *live = lv;
+    *total = p.nalm * (int64_t)p.nslots;
+    return SHT_OK;
 }
 
 sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int64_t *nphi, const double *theta,

@@ -36,13 +36,15 @@ EXPORTS = (
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
     "sht_plan_set_tuning", "sht_plan_tuning", "sht_plan_selftest_timeout", "sht_alm2map_ws", "sht_map2alm_ws",
+    "sht_plan_live_steps",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
 TUNE_SYNTH_MAPS, TUNE_ANAL_MAPS, TUNE_ANAL_SLOTS, TUNE_DF_MAPS, TUNE_TC_MAPS, TUNE_PREC_ANAL, TUNE_PREC_RING = range(7)
 TUNE_VALUES = {TUNE_SYNTH_MAPS: (1, 2, 4), TUNE_ANAL_MAPS: (1, 2), TUNE_ANAL_SLOTS: (1, 4),
                TUNE_DF_MAPS: (4, 8, 16), TUNE_TC_MAPS: (8, 16), TUNE_PREC_ANAL: (0, 1), TUNE_PREC_RING: (0, 1)}
-STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce")
+STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce", "tc_synth_kernel",
+          "tc_anal_kernel")
 
 
 class ShtError(RuntimeError):
@@ -92,6 +94,7 @@ def load():
             "sht_noalloc_scratch_bytes": (S, []),
             "sht_plan_set_mode": (I, [P, I]),
             "sht_plan_mode": (I, [P]),
+            "sht_plan_live_steps": (I, [P, P, P]),
             "sht_plan_device_status": (I, [P, P, I]),
             "sht_plan_reserve": (I, [P, I]),
             "sht_plan_set_tuning": (I, [P, I, I]),
@@ -230,6 +233,14 @@ class Plan:
             _check(st, self._h)
         return int(v.value)
 
+    def live_steps(self):
+        """(live, total) recurrence steps of one pass: total = nalm * slots; live from the first
+        32-l chunk per (m, 128-slot block) with a value above the dropping threshold (needs the
+        precision-form tables: call set_mode(MODE_SPLIT_BF16) once first)."""
+        lv, tot = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sht_plan_live_steps(self._h, ctypes.byref(lv), ctypes.byref(tot)), self._h)
+        return int(lv.value), int(tot.value)
+
     def selftest_timeout(self, stream=None):
         """Run the failure path of the device waits once (sets bit 0 of the status word)."""
         _check(load().sht_plan_selftest_timeout(self._h, _stream_ptr(stream)), self._h)
@@ -239,8 +250,8 @@ class Plan:
 
     def stage_times(self, reset: bool = False):
         """{stage: (ms, launches)} accumulated since the last reset (waits for the recorded events)."""
-        ms = np.zeros(5, np.float64)
-        nl = np.zeros(5, np.int64)
+        ms = np.zeros(len(STAGES), np.float64)
+        nl = np.zeros(len(STAGES), np.int64)
         _check(load().sht_plan_stage_times(self._h, _np_ptr(ms), _np_ptr(nl), 1 if reset else 0), self._h)
         return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(STAGES)}
 

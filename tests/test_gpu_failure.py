@@ -26,3 +26,16 @@ def test_bounded_wait_times_out_and_context_survives():
     assert torch.equal(p.alm2map(a), before)         # the context still runs transforms
     p.set_mode(sht.MODE_SPLIT_BF16)
     assert p.map2alm(before).shape == (2, p.nalm) and p.device_status() == 0
+
+
+def test_status_read_waits_for_work_on_a_nonblocking_stream():
+    """The status read synchronises the whole device: a timeout recorded by a kernel still running
+    on a non-blocking stream (torch's pool streams are) is seen without a manual synchronize."""
+    from paper_1106_0159_gb300 import sht
+    p = sht.Plan(sht.healpix_geometry(16), 32, 32, grid=sht.GRID_HEALPIX)
+    assert p.device_status() == 0
+    side = torch.cuda.Stream()
+    p.selftest_timeout(stream=side)
+    assert p.device_status(clear=True) & 1
+    assert p.device_status() == 0
+    p.close()

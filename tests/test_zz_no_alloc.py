@@ -4,7 +4,8 @@ framework's memory pool or under a fixed memory budget, or that must avoid
 the device synchronisation an allocation can cause).  Its scratch is a static
 device array, so the call itself allocates nothing.  Its output must agree
 with sht_alm2map's, on two calls in a row (the second reuses the array the
-first one left behind).  This file is collected last on purpose."""
+first one left behind), and it runs the plan's own arithmetic (FP64 or the
+precision form).  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -49,6 +50,34 @@ def test_noalloc_matches_alm2map_on_two_calls_in_a_row():
         assert _rel(got, want) <= TOL
         outs.append(got)
     assert not np.array_equal(outs[0], outs[1])
+    plan.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_noalloc_runs_the_plan_mode_and_matches_the_oracle(mode):
+    """HEALPix Nside 32, lmax 64, one map (the smallest benchmark configuration): the no-alloc
+    synthesis takes the plan's own arithmetic, so on a precision-form plan it gives exactly what
+    sht_alm2map gives there, and in either mode it matches the oracle's pixel-by-pixel synthesis
+    within that mode's tolerance (1e-11 FP64, 1e-9 precision form)."""
+    import oracle
+    from oracle import geometry
+    from paper_1106_0159_gb300 import sht
+    lib = sht.load()
+    L, nside = 64, 32
+    geom = geometry.healpix(nside)
+    plan = sht.Plan(geom, L, L, grid=sht.GRID_HEALPIX)
+    if mode == "split":
+        plan.set_mode(sht.MODE_SPLIT_BF16)
+    a_h = inputs.gaussian_alm(L, L, seed=43, nmaps=1)
+    a = torch.from_numpy(a_h).cuda()
+    ref = plan.alm2map(a)
+    out = torch.full_like(ref, float("nan"))
+    for _ in range(2):
+        assert _call(lib, plan, a, out) == sht.SHT_OK, lib.sht_plan_last_error(plan._h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    want = oracle.alm2map_exact(geom, a_h[0], L, L)
+    assert _rel(out.cpu().numpy()[0], want) <= (TOL if mode == "fp64" else 1e-9)
     plan.close()
 
 
