@@ -26,18 +26,20 @@ from . import geometry  # noqa: F401  (re-exported)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sht_oracle.c")
+_SPIN_SRC = os.path.join(_HERE, "spin_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``sht_oracle.c`` into ``liboracle.so`` with gcc (OpenMP, -O2, no fast-math)."""
+    """Compile ``sht_oracle.c`` and ``spin_oracle.c`` into ``liboracle.so`` with gcc (OpenMP, -O2,
+    no fast-math)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SPIN_SRC))):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, _SPIN_SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -61,6 +63,11 @@ def _load():
             "oracle_map2alm_exact": [I, P, P, P, P, I, I, P, P],
             "oracle_delta_anal": [I, P, P, P, P, I, P, P],
             "oracle_legendre_anal": [I, P, I, I, P, P, P],
+            "oracle_spin_lambda": [D, I, I, I, P],
+            "oracle_spin_delta_synth": [I, P, I, I, P, P, I, P, P, P],
+            "oracle_spin_legendre_anal": [I, P, I, I, P, P, P, P, P],
+            "oracle_spin_alm2map_exact": [I, P, P, P, I, I, P, P, P, P],
+            "oracle_spin_map2alm_exact": [I, P, P, P, P, I, I, P, P, P, P],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -213,3 +220,90 @@ def map2alm_rings(geom, m_, lmax: int, mmax: int) -> np.ndarray:
     ms = np.arange(mmax + 1)
     parts = map2alm_ms(geom, m_, lmax, ms)
     return np.concatenate(parts)
+
+
+# ---------------------------------------------------------------- spin-weighted (spin 2)
+#
+# Polarisation maps (Q, U) and coefficients (E, B) as defined at the top of spin_oracle.c:
+# Q + iU = sum 2a_lm 2Y_lm with 2a_lm = -(E_lm + i B_lm), the analysis with conj(Y) and the ring
+# weights.  Arrays: E, B complex m-major triangles (the first l = 0, 1 entries are ignored on input
+# and zero on output); Q, U real [npix] in ring order.
+
+
+def spin_lambda(theta: float, lmax: int, m: int, s: int) -> np.ndarray:
+    """slambda_{l m}(theta) for l = m..lmax (zero for l < max(m, |s|))."""
+    out = np.zeros(lmax - m + 1, dtype=np.float64)
+    _load().oracle_spin_lambda(float(theta), int(lmax), int(m), int(s), _p(out))
+    return out
+
+
+def spin_delta_synth(geom, E, B, lmax: int, mmax: int, rings=None):
+    """Delta^Q_m(r), Delta^U_m(r) of the spin-2 synthesis, each [len(rings)][mmax+1] complex."""
+    nphi, theta, phi0, w = geom
+    theta = _f64(theta)
+    rings = _i32(np.arange(len(theta)) if rings is None else rings)
+    E, B = _c128(E), _c128(B)
+    assert E.size == nalm(lmax, mmax) and B.size == E.size
+    dq = np.zeros((len(rings), mmax + 1), dtype=np.complex128)
+    du = np.zeros_like(dq)
+    _load().oracle_spin_delta_synth(len(theta), _p(theta), lmax, mmax, _p(E), _p(B), len(rings), _p(rings),
+                                    _p(dq), _p(du))
+    return dq, du
+
+
+def spin_alm2map_rings(geom, E, B, lmax: int, mmax: int, rings=None):
+    """Separable spin-2 synthesis of the selected rings: (Q, U) pixels, concatenated by ring."""
+    rings = np.arange(len(geom[0])) if rings is None else np.asarray(rings)
+    dq, du = spin_delta_synth(geom, E, B, lmax, mmax, rings)
+    return ring_synth(geom, dq, mmax, rings), ring_synth(geom, du, mmax, rings)
+
+
+def spin_map2alm_ms(geom, q, u, lmax: int, ms):
+    """Separable spin-2 analysis for the selected m: lists of E_{l m} and B_{l m}, l = m..lmax."""
+    nphi, theta, phi0, w = geom
+    theta = _f64(theta)
+    ms = _i32(ms)
+    dq = delta_anal(geom, q, ms)
+    du = delta_anal(geom, u, ms)
+    sizes = [lmax - int(m) + 1 for m in ms]
+    E = np.zeros(sum(sizes), dtype=np.complex128)
+    B = np.zeros_like(E)
+    _load().oracle_spin_legendre_anal(len(theta), _p(theta), lmax, len(ms), _p(ms), _p(_c128(dq)), _p(_c128(du)),
+                                      _p(E), _p(B))
+    outE, outB, o = [], [], 0
+    for sz in sizes:
+        outE.append(E[o:o + sz].copy())
+        outB.append(B[o:o + sz].copy())
+        o += sz
+    return outE, outB
+
+
+def spin_map2alm_rings(geom, q, u, lmax: int, mmax: int):
+    """Separable spin-2 analysis for every m, as full m-major E and B vectors."""
+    E, B = spin_map2alm_ms(geom, q, u, lmax, np.arange(mmax + 1))
+    return np.concatenate(E), np.concatenate(B)
+
+
+def spin_alm2map_exact(geom, E, B, lmax: int, mmax: int):
+    """Pixel-by-pixel spin-2 synthesis from the definition: (Q, U)."""
+    nphi, theta, phi0, w = geom
+    nphi, theta, phi0 = _i64(nphi), _f64(theta), _f64(phi0)
+    E, B = _c128(E), _c128(B)
+    assert E.size == nalm(lmax, mmax) and B.size == E.size
+    q = np.zeros(int(nphi.sum()), dtype=np.float64)
+    u = np.zeros_like(q)
+    _load().oracle_spin_alm2map_exact(len(nphi), _p(nphi), _p(theta), _p(phi0), lmax, mmax, _p(E), _p(B), _p(q), _p(u))
+    return q, u
+
+
+def spin_map2alm_exact(geom, q, u, lmax: int, mmax: int):
+    """Pixel-by-pixel spin-2 analysis from the definition: (E, B)."""
+    nphi, theta, phi0, w = geom
+    nphi, theta, phi0, w = _i64(nphi), _f64(theta), _f64(phi0), _f64(w)
+    q, u = _f64(q), _f64(u)
+    assert q.size == nphi.sum() and u.size == q.size
+    E = np.zeros(nalm(lmax, mmax), dtype=np.complex128)
+    B = np.zeros_like(E)
+    _load().oracle_spin_map2alm_exact(len(nphi), _p(nphi), _p(theta), _p(phi0), _p(w), lmax, mmax, _p(q), _p(u),
+                                      _p(E), _p(B))
+    return E, B
