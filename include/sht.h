@@ -159,6 +159,29 @@ sht_status sht_alm2map_ws(sht_plan_t plan, const void *alm, double *map, int nma
 sht_status sht_map2alm_ws(sht_plan_t plan, const double *map, void *alm, int nmaps, void *stream, void *scratch,
                           size_t scratch_bytes);
 
+/*
+ * Spin-weighted (polarisation) transforms, the extension the paper names as future work
+ * (Section 6), on the same plan and grid.  Only spin = 2 is implemented (SHT_EUNSUPPORTED
+ * otherwise).  Functions sY_lm = slambda_lm(theta) exp(i m phi) in the normalisation of the scalar
+ * lambda_lm (no Condon-Shortley factor): slambda_lm = sqrt((l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!))
+ * sum_r C(l-s, r) C(l+s, r+s-m) (-1)^(l-r-s) sin(theta/2)^(2l-2r-s+m) cos(theta/2)^(2r+s-m).
+ * Maps Q, U and coefficients E_lm, B_lm (l >= 2; entries with l < 2 are ignored on input and written
+ * as 0; Im at m = 0 likewise):
+ *   synthesis  Q + iU = sum_{l >= 2} sum_{|m| <= l} -(E_lm + i B_lm) 2Y_lm,
+ *              with E_{l,-m} = (-1)^m conj(E_lm), B likewise (real Q, U);
+ *   analysis   E_lm = -(2a_lm + 2a'_lm)/2, B_lm = i (2a_lm - 2a'_lm)/2 with
+ *              2a_lm = sum_r w_r sum_j (Q + iU) conj(2Y_lm), 2a'_lm = sum_r w_r sum_j (Q - iU) conj((-2)Y_lm).
+ * Layouts: alm complex128 [nmaps][2][nalm] (E then B, m-major triangle as above); map double
+ * [nmaps][2][npix] (Q then U).  Arithmetic is FP64 for the Legendre step whatever the plan's mode
+ * (the ring DFTs follow the mode, as in the scalar transforms); no Reinsch form on polar rings.
+ * The first spin call on a plan builds its spin recurrence tables on the host and copies them to
+ * the device (synchronous; 32 nalm bytes): make it before any stream capture.  Scratch grows on
+ * demand to sht_spin_workspace_bytes(plan, nmaps).  Stream ordering and errors as sht_alm2map.
+ */
+sht_status sht_alm2map_spin(sht_plan_t plan, int spin, const void *alm, double *map, int nmaps, void *stream);
+sht_status sht_map2alm_spin(sht_plan_t plan, int spin, const double *map, void *alm, int nmaps, void *stream);
+size_t     sht_spin_workspace_bytes(sht_plan_t plan, int nmaps);
+
 /* The four stages on their own (same layouts; delta as documented above). */
 sht_status sht_legendre_synth(sht_plan_t plan, const void *alm, void *delta, int nmaps, void *stream); /* eq. DeltaDef */
 sht_status sht_ring_synth(sht_plan_t plan, const void *delta, double *map, int nmaps, void *stream);    /* eq. Delta2map */

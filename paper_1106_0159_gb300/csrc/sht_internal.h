@@ -79,6 +79,8 @@ struct Plan {
     double2 *d_tc_ck_y = nullptr;       // [mmax + 1][slot blocks][128] recurrence state at the first live chunk & ~1
     int *d_tc_ck_k = nullptr;           // its rescaling exponents
     int *d_status = nullptr;            // device status word (bounded waits that gave up)
+    double4 *d_spin_tab = nullptr;      // spin 2: [nalm] (alpha, alpha (1 + g), alpha (1 - g), c), built on first use
+    double *d_spin_start = nullptr;     // spin 2: [mmax + 1] start coefficients S_m
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
     // launch tuning (sht_tune): maps or slots per thread per launch
@@ -165,6 +167,14 @@ cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 
 // precision-form synthesis of the polar slots 0 .. 127 for m <= mR (Reinsch form, double-float sums)
 cudaError_t launch_legendre_synth_df_polar(const Plan &p, const double2 *alm, double2 *delta, int nmaps,
                                            cudaStream_t st, int *nlaunch);
+
+// spin-2 transforms (spin.cu): Legendre steps on [nmaps][2] coefficient / Delta pairs
+cudaError_t build_spin_tables(Plan &p);
+size_t spin_partial_bytes(const Plan &p, int nmaps);
+cudaError_t launch_spin_synth(const Plan &p, const double2 *alm, double2 *delta, int nmaps, cudaStream_t st,
+                              int *nlaunch);
+cudaError_t launch_spin_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
+                             cudaStream_t st, int *nlaunch);
 
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st);

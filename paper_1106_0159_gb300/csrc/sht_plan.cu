@@ -71,7 +71,7 @@ void free_plan_device(Plan &p)
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
                     p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
                     p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df,
-                    p.d_tc_ck_y, p.d_tc_ck_k};
+                    p.d_tc_ck_y, p.d_tc_ck_k, p.d_spin_tab, p.d_spin_start};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -92,6 +92,8 @@ void free_plan_device(Plan &p)
     p.d_phase_df = nullptr;
     p.d_tc_ck_y = nullptr;
     p.d_tc_ck_k = nullptr;
+    p.d_spin_tab = nullptr;
+    p.d_spin_start = nullptr;
     p.ws_bytes = 0;
 }
 
@@ -672,6 +674,72 @@ sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps,
     return run_legendre_anal(p, delta, (double2 *)alm, scratch, nmaps, s);
 }
 
+// Spin-2 transforms (see the header and spin.cu).
+static sht_status spin_prepare(Plan &p, int spin)
+{
+    if (spin != 2) {
+        p.last_error = "spin-weighted transforms: only spin 2 is implemented";
+        return SHT_EUNSUPPORTED;
+    }
+    cudaError_t e = sht::build_spin_tables(p);
+    if (e != cudaSuccess) return cuda_fail(p, e, "spin tables");
+    return SHT_OK;
+}
+
+size_t sht_spin_workspace_bytes(sht_plan_t plan, int nmaps)
+{
+    if (!plan || nmaps <= 0) return 0;
+    const Plan &p = plan->p;
+    return align256(delta_bytes(p, 2 * nmaps)) +
+           std::max(align256(sht::ring_scratch_bytes(p)), align256(sht::spin_partial_bytes(p, std::min(nmaps, 2))));
+}
+
+sht_status sht_alm2map_spin(sht_plan_t plan, int spin, const void *alm, double *map, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, alm, map, nmaps);
+    if (st != SHT_OK) return st;
+    Plan &p = plan->p;
+    if ((st = spin_prepare(p, spin)) != SHT_OK || nmaps == 0) return st;
+    st = ensure_workspace(p, sht_spin_workspace_bytes(plan, nmaps));
+    if (st != SHT_OK) return st;
+    const size_t d = align256(delta_bytes(p, 2 * nmaps));
+    double2 *delta = (double2 *)p.d_ws;
+    double2 *scratch = (double2 *)((char *)p.d_ws + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        StageScope sc(p, SHT_STAGE_LEGENDRE_SYNTH, s);
+        int n = 0;
+        cudaError_t e = sht::launch_spin_synth(p, (const double2 *)alm, delta, nmaps, s, &n);
+        p.launches[SHT_STAGE_LEGENDRE_SYNTH] += n;
+        if (e != cudaSuccess) return cuda_fail(p, e, "spin legendre_synth");
+        sc.done();
+    }
+    return run_ring_synth(p, delta, map, scratch, 2 * nmaps, s);
+}
+
+sht_status sht_map2alm_spin(sht_plan_t plan, int spin, const double *map, void *alm, int nmaps, void *stream)
+{
+    sht_status st = check_call(plan, map, alm, nmaps);
+    if (st != SHT_OK) return st;
+    Plan &p = plan->p;
+    if ((st = spin_prepare(p, spin)) != SHT_OK || nmaps == 0) return st;
+    st = ensure_workspace(p, sht_spin_workspace_bytes(plan, nmaps));
+    if (st != SHT_OK) return st;
+    const size_t d = align256(delta_bytes(p, 2 * nmaps));
+    double2 *delta = (double2 *)p.d_ws;
+    double2 *scratch = (double2 *)((char *)p.d_ws + d);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_ring_anal(p, map, delta, scratch, 2 * nmaps, s);
+    if (st != SHT_OK) return st;
+    StageScope sc(p, SHT_STAGE_LEGENDRE_ANAL, s);
+    int n = 0;
+    cudaError_t e = sht::launch_spin_anal(p, delta, (double2 *)alm, scratch, nmaps, s, &n);
+    p.launches[SHT_STAGE_LEGENDRE_ANAL] += n;
+    if (e != cudaSuccess) return cuda_fail(p, e, "spin legendre_anal");
+    sc.done();
+    return SHT_OK;
+}
+
 // The same transforms on caller-owned scratch (see the header).
 static sht_status check_ws(sht_plan_t plan, int nmaps, void *scratch, size_t scratch_bytes)
 {
@@ -779,53 +847,70 @@ sht_status sht_geom_healpix(int nside, int64_t *nphi, double *theta, double *phi
     return SHT_OK;
 }
 
-// Gauss-Legendre nodes by Newton's method on P_N from the asymptotic guess,
-// weights 2 / ((1 - x^2) P_N'(x)^2); the southern half mirrors the northern one.
+// Gauss-Legendre nodes by Newton's method on P_N(cos theta) in the colatitude itself, from the
+// asymptotic guess theta = pi (j + 3/4) / (N + 1/2); weights 2 sin^2(theta) / (N P_{N-1}(x))^2
+// (at a root, (1 - x^2) P_N'(x) = N P_{N-1}(x)), with no 1 - x^2 cancellation near the poles.
+// The southern half mirrors the northern one.
+static void legendre_pair(int N, double th, double &pn, double &pn1)
+{
+    if (N == 0) {
+        pn = 1.0;
+        pn1 = 0.0;
+        return;
+    }
+    const double x = std::cos(th);
+    double p0 = 1.0, p1 = x;  // P_{l-1}, P_l
+    if (x > 0.5) {
+        // near the pole: Reinsch's difference form with u = 1 - x = 2 sin^2(theta/2) exact, so that
+        // rounding acts on D_l = P_l - P_{l-1}:  D_{l+1} = (l D_l - (2l+1) u P_l) / (l+1)
+        const double h = std::sin(0.5 * th);
+        const double u = 2.0 * h * h;
+        p1 = 1.0 - u;
+        double d = -u;
+        for (int l = 1; l < N; ++l) {
+            d = (l * d - (2.0 * l + 1.0) * u * p1) / (l + 1.0);
+            p0 = p1;
+            p1 += d;
+        }
+    } else {
+        for (int l = 1; l < N; ++l) {
+            const double p2 = ((2.0 * l + 1.0) * x * p1 - l * p0) / (l + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+    }
+    pn = p1;
+    pn1 = p0;
+}
+
 sht_status sht_geom_gauss_legendre(int nrings, int64_t nphi, int64_t *nphi_out, double *theta, double *phi0, double *w)
 {
     if (nrings < 1 || nrings > (1 << 16) || nphi < 1 || nphi > (1 << 20) || !nphi_out || !theta || !phi0 || !w)
         return SHT_EINVAL;
     const int N = nrings;
     for (int j = 0; j < (N + 1) / 2; ++j) {
-        double x = std::cos(PI * (j + 0.75) / (N + 0.5));
-        double dp = 1.0;
-        int converged = 0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int l = 2; l <= N; ++l) {
-                const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
-                p0 = p1;
-                p1 = p2;
-            }
-            if (N == 1) {
-                p1 = x;
-                p0 = 1.0;
-            }
-            dp = N * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (std::fabs(dx) < 1e-15) {
-                if (++converged >= 2) break;
-            }
-        }
-        // final derivative at the converged node
-        {
-            double p0 = 1.0, p1 = x;
-            for (int l = 2; l <= N; ++l) {
-                const double p2 = ((2.0 * l - 1.0) * x * p1 - (l - 1.0) * p0) / l;
-                p0 = p1;
-                p1 = p2;
-            }
-            if (N == 1) {
-                p1 = x;
-                p0 = 1.0;
-            }
-            dp = N * (x * p1 - p0) / (x * x - 1.0);
-        }
-        const double wg = 2.0 / ((1.0 - x * x) * dp * dp);
         const int js = N - 1 - j;
-        if (js == j) x = 0.0;
-        const double th = std::acos(x);
+        double th = PI * (j + 0.75) / (N + 0.5);
+        if (js == j) {
+            th = 0.5 * PI;  // odd N: the equator is a node
+        } else {
+            int converged = 0;
+            for (int it = 0; it < 100; ++it) {
+                const double x = std::cos(th), sn = std::sin(th);
+                double pn, pn1;
+                legendre_pair(N, th, pn, pn1);
+                // d P_N(cos theta) / d theta = -N (P_{N-1} - x P_N) / sin(theta)
+                const double dth = pn * sn / (N * (pn1 - x * pn));
+                th += dth;
+                if (std::fabs(dth) <= 1e-16 * th) {
+                    if (++converged >= 2) break;
+                }
+            }
+        }
+        const double sn = std::sin(th);
+        double pn, pn1;
+        legendre_pair(N, th, pn, pn1);
+        const double wg = 2.0 * sn * sn / ((N * pn1) * (N * pn1));
         theta[j] = th;
         w[j] = 2.0 * PI * wg / (double)nphi;
         if (js != j) {

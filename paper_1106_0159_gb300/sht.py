@@ -36,7 +36,7 @@ EXPORTS = (
     "sht_fp64_fma_tflops", "sht_alm2map_noalloc", "sht_noalloc_scratch_bytes",
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
     "sht_plan_set_tuning", "sht_plan_tuning", "sht_plan_selftest_timeout", "sht_alm2map_ws", "sht_map2alm_ws",
-    "sht_plan_live_steps",
+    "sht_plan_live_steps", "sht_alm2map_spin", "sht_map2alm_spin", "sht_spin_workspace_bytes",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
@@ -95,6 +95,9 @@ def load():
             "sht_plan_set_mode": (I, [P, I]),
             "sht_plan_mode": (I, [P]),
             "sht_plan_live_steps": (I, [P, P, P]),
+            "sht_alm2map_spin": (I, [P, I, P, P, I, P]),
+            "sht_map2alm_spin": (I, [P, I, P, P, I, P]),
+            "sht_spin_workspace_bytes": (S, [P, I]),
             "sht_plan_device_status": (I, [P, P, I]),
             "sht_plan_reserve": (I, [P, I]),
             "sht_plan_set_tuning": (I, [P, I, I]),
@@ -323,6 +326,26 @@ class Plan:
         s = self._dev(m, torch.float64, (self.npix,), "map")
         o = self._out(out, (s.shape[0], self.nalm), torch.complex128, s)
         self._run(load().sht_map2alm, s, o, s.shape[0], stream)
+        return o
+
+    def alm2map_spin(self, alm, out=None, stream=None, spin: int = 2):
+        """Spin-2 synthesis: [nmaps, 2, nalm] complex128 (E, B) -> [nmaps, 2, npix] float64 (Q, U)."""
+        import torch
+        a = self._dev(alm, torch.complex128, (2, self.nalm), "alm")
+        o = self._out(out, (a.shape[0], 2, self.npix), torch.float64, a)
+        st = load().sht_alm2map_spin(self._h, int(spin), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                     int(a.shape[0]), _stream_ptr(stream))
+        _check(st, self._h, "sht_alm2map_spin")
+        return o
+
+    def map2alm_spin(self, m, out=None, stream=None, spin: int = 2):
+        """Spin-2 analysis: [nmaps, 2, npix] float64 (Q, U) -> [nmaps, 2, nalm] complex128 (E, B)."""
+        import torch
+        s = self._dev(m, torch.float64, (2, self.npix), "map")
+        o = self._out(out, (s.shape[0], 2, self.nalm), torch.complex128, s)
+        st = load().sht_map2alm_spin(self._h, int(spin), ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(o.data_ptr()),
+                                     int(s.shape[0]), _stream_ptr(stream))
+        _check(st, self._h, "sht_map2alm_spin")
         return o
 
     def scratch(self, nmaps: int):

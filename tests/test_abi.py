@@ -59,9 +59,10 @@ def test_gauss_legendre_helper_matches_scipy(n):
     b = geometry.gauss_legendre(n, 2 * n + 1)
     assert np.array_equal(a[0], b[0])
     assert np.max(np.abs(np.cos(a[1]) - np.cos(b[1]))) < 2e-15
-    # the helper works in double: 1 - x^2 at the polar node of n = 2049 (x ~ 1 - 7e-7)
-    # carries ~1e-10 relative error; the oracle's nodes are polished in long double
-    assert np.max(np.abs(a[3] - b[3]) / b[3]) < 2e-10
+    # the helper works in double, with Newton's method in theta and Reinsch's difference form of
+    # the Legendre recurrence near the poles; the oracle's nodes are polished in long double
+    assert np.max(np.abs(a[1] - b[1]) / b[1]) < 1e-13
+    assert np.max(np.abs(a[3] - b[3]) / b[3]) < 2e-12
     assert np.allclose(a[1] + a[1][::-1], math.pi, atol=1e-15, rtol=0)
     # what the transforms need: exact quadrature of P_l for l < 2n
     sp = pytest.importorskip("scipy.special")
@@ -109,6 +110,11 @@ def test_plan_create_rejects_bad_arguments_before_device_work():
     assert lib.sht_plan_selftest_timeout(None, None) == sht.SHT_EINVAL
     assert lib.sht_alm2map_ws(None, None, None, 1, None, None, 0) == sht.SHT_EINVAL
     assert lib.sht_map2alm_ws(None, None, None, 1, None, None, 0) == sht.SHT_EINVAL
+    assert lib.sht_alm2map_spin(None, 2, None, None, 1, None) == sht.SHT_EINVAL
+    assert lib.sht_map2alm_spin(None, 2, None, None, 1, None) == sht.SHT_EINVAL
+    assert lib.sht_spin_workspace_bytes(None, 1) == 0
+    lv, tot = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.sht_plan_live_steps(None, ctypes.byref(lv), ctypes.byref(tot)) == sht.SHT_EINVAL
     assert lib.sht_status_string(sht.SHT_EINVAL) == b"invalid argument"
     assert lib.sht_plan_last_error(None) == b""
 
