@@ -111,6 +111,19 @@ int        sht_plan_mode(sht_plan_t plan);
 sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear);
 
 /*
+ * Restrict the FP64 Legendre steps of the plan to the listed m (the per-rank work of an
+ * m-sharded transform, Section 4.1: the Legendre step of rank r covers its m and every ring, the
+ * ring step its rings and every m).  With a list set, sht_legendre_synth / sht_alm2map compute
+ * Delta_m only for listed m and write Delta_m = 0 for the others (a_lm of unlisted m is read as
+ * zero), and sht_legendre_anal / sht_map2alm write a_lm = 0 for unlisted m.  The ring stages are
+ * unchanged.  ms: host array of n distinct values in [0, mmax] (copied); n = 0 (ms may be NULL)
+ * clears the list.  While a list is set, precision-form Legendre calls and the spin transforms
+ * return SHT_EUNSUPPORTED.  Host call (synchronous copy of a flag table); SHT_EINVAL for a bad
+ * list, which leaves the previous one in place.
+ */
+sht_status sht_plan_set_mlist(sht_plan_t plan, const int *ms, int n);
+
+/*
  * Work accounting (host call, synchronous): the (l, m, ring-slot) recurrence steps of one pass,
  * *total = nalm * slots, and *live, those from the first 32-l chunk of each (m, block of 128
  * slots) in which some lambda is above the 2^-256 dropping threshold of the rescaling scheme

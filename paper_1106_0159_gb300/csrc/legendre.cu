@@ -113,6 +113,7 @@ struct SynArgs {
     const double *u, *s;
     const double *alpha, *cfac;
     const double3 *rein;  // Reinsch coefficients for m <= mR
+    const int *mflag;     // [mmax+1] 1 for the m this plan computes (null: all)
     int nslots, nblk, lmax, mmax, nrings, mR;
     int64_t nalm;
 };
@@ -234,6 +235,19 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
     __shared__ double2 s_a[NM][CHL];
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
+    if (A.mflag && !A.mflag[m]) {  // an m this plan does not compute: Delta_m = 0 on these rings
+        const int slot = blk * SYN_T + threadIdx.x;
+        if (slot < A.nslots) {
+            const int rn = A.slotN[slot], rs = A.slotS[slot];
+            const int64_t mstride = A.mmax + 1;
+            for (int g = 0; g < NM; ++g) {
+                double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
+                if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
+                if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
+            }
+        }
+        return;
+    }
     const bool polar = m <= A.mR && A.s[blk * SYN_T] < POLAR_SIN;  // slots are sorted by colatitude
     if (polar)
         synth_body<NM, true>(A, m, blk, C, s_a);
@@ -248,6 +262,7 @@ struct AnaArgs {
     const double *u, *s;
     const double *alpha, *cfac;
     const double3 *rein;
+    const int *mflag;      // [mmax+1] 1 for the m this plan computes (null: all)
     int nslots, nblk, lmax, mmax, nrings, mR;
     int64_t nalm;
     int64_t part_map_stride;   // nalm
@@ -430,6 +445,15 @@ __global__ void __launch_bounds__(ANA_T) legendre_anal_kernel(AnaArgs A)
     __shared__ double s_red[NW][CHL][2 * NM];
     const int m = blockIdx.x / A.nblk;
     const int blk = blockIdx.x - m * A.nblk;
+    if (A.mflag && !A.mflag[m]) {  // an m this plan does not compute: zero partials
+        const int64_t base = (int64_t)m * (2 * A.lmax + 3 - m) / 2;
+        for (int i = threadIdx.x; i < (A.lmax - m + 1) * NM; i += ANA_T) {
+            const int j = i % (A.lmax - m + 1), g = i / (A.lmax - m + 1);
+            A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + base + j] =
+                make_double2(0.0, 0.0);
+        }
+        return;
+    }
     const bool polar = m <= A.mR && A.s[blk * (ANA_T * K)] < POLAR_SIN;
     if (polar)
         anal_body<NM, K, true>(A, m, blk, C, s_red);
@@ -472,6 +496,7 @@ cudaError_t launch_legendre_synth(const Plan &p, const double2 *alm, double2 *de
     A.alpha = p.d_alpha;
     A.cfac = p.d_cfac;
     A.rein = p.d_rein;
+    A.mflag = p.d_mflag;
     A.mR = p.mR;
     A.nslots = p.nslots;
     A.nblk = (p.nslots + SYN_T - 1) / SYN_T;
@@ -532,6 +557,7 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *p
     A.alpha = p.d_alpha;
     A.cfac = p.d_cfac;
     A.rein = p.d_rein;
+    A.mflag = p.d_mflag;
     A.mR = p.mR;
     A.nslots = p.nslots;
     A.nblk = (p.nslots + per - 1) / per;

@@ -58,6 +58,10 @@ extern "C" sht_status sht_alm2map_noalloc(sht_plan_t plan, const void *alm, doub
     if (!alm || !map || alm == (const void *)map) return SHT_EINVAL;
     sht::Plan &p = plan->p;
     const bool prec = p.mode == SHT_MODE_SPLIT_BF16;
+    if (prec && p.n_mlist > 0) {
+        p.last_error = "sht_alm2map_noalloc: an m list is set: only the FP64 Legendre step computes a subset of m";
+        return SHT_EUNSUPPORTED;
+    }
     const size_t delta = ((size_t)nmaps * p.nrings * (p.mmax + 1) * sizeof(double2) + 255) & ~(size_t)255;
     const size_t per_cta = (size_t)3 * p.fft_maxlen * sizeof(double2);
     // the precision form's digit tiles of c_lm a_lm share the region after Delta with the ring

@@ -79,6 +79,8 @@ struct Plan {
     double2 *d_tc_ck_y = nullptr;       // [mmax + 1][slot blocks][128] recurrence state at the first live chunk & ~1
     int *d_tc_ck_k = nullptr;           // its rescaling exponents
     int *d_status = nullptr;            // device status word (bounded waits that gave up)
+    int *d_mflag = nullptr;             // [mmax + 1] m computed by the FP64 Legendre steps (null: all)
+    int n_mlist = 0;                    // number of listed m (0: all)
     double4 *d_spin_tab = nullptr;      // spin 2: [nalm] (alpha, alpha (1 + g), alpha (1 - g), c), built on first use
     double *d_spin_start = nullptr;     // spin 2: [mmax + 1] start coefficients S_m
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)

@@ -71,7 +71,7 @@ void free_plan_device(Plan &p)
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
                     p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
                     p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df,
-                    p.d_tc_ck_y, p.d_tc_ck_k, p.d_spin_tab, p.d_spin_start};
+                    p.d_tc_ck_y, p.d_tc_ck_k, p.d_spin_tab, p.d_spin_start, p.d_mflag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -94,6 +94,8 @@ void free_plan_device(Plan &p)
     p.d_tc_ck_k = nullptr;
     p.d_spin_tab = nullptr;
     p.d_spin_start = nullptr;
+    p.d_mflag = nullptr;
+    p.n_mlist = 0;
     p.ws_bytes = 0;
 }
 
@@ -265,9 +267,19 @@ using sht::StageEvents;
 using StageScope = StageEvents;
 
 // tc_scratch: tc_workspace_bytes(p, min(nmaps, 16)) bytes, used in the precision form only
+sht_status mlist_guard(Plan &p)
+{
+    if (p.n_mlist > 0 && p.mode != SHT_MODE_FP64) {
+        p.last_error = "an m list is set: only the FP64 Legendre steps compute a subset of m";
+        return SHT_EUNSUPPORTED;
+    }
+    return SHT_OK;
+}
+
 sht_status run_legendre_synth(Plan &p, const double2 *alm, double2 *delta, void *tc_scratch, int nmaps,
                               cudaStream_t s)
 {
+    if (sht_status g = mlist_guard(p)) return g;
     StageScope sc(p, 0, s);
     int n = 0;
     cudaError_t e;
@@ -322,6 +334,7 @@ sht_status run_ring_anal(Plan &p, const double *map, double2 *delta, double2 *sc
 sht_status run_legendre_anal(Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
                              cudaStream_t s)
 {
+    if (sht_status g = mlist_guard(p)) return g;
     if (p.mode == SHT_MODE_SPLIT_BF16) {
         // precision form (reduction included): the l-sum contraction on the tensor cores, or
         // double-float products and slot sums on the FP32 pipe
@@ -456,6 +469,37 @@ sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
     if (e == cudaSuccess && clear) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(p, e, "device status");
     return (*status & 1) ? SHT_ETIMEOUT : SHT_OK;
+}
+
+sht_status sht_plan_set_mlist(sht_plan_t plan, const int *ms, int n)
+{
+    if (!plan || n < 0 || (n > 0 && !ms)) return SHT_EINVAL;
+    Plan &p = plan->p;
+    if (n == 0) {
+        if (p.d_mflag) {
+            cudaError_t e = cudaFree(p.d_mflag);
+            p.d_mflag = nullptr;
+            if (e != cudaSuccess) return cuda_fail(p, e, "m list");
+        }
+        p.n_mlist = 0;
+        return SHT_OK;
+    }
+    std::vector<int> flag((size_t)p.mmax + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if (ms[i] < 0 || ms[i] > p.mmax || flag[ms[i]]) return SHT_EINVAL;
+        flag[ms[i]] = 1;
+    }
+    if (!p.d_mflag) {
+        cudaError_t e = cudaMalloc(&p.d_mflag, sizeof(int) * flag.size());
+        if (e != cudaSuccess) {
+            p.d_mflag = nullptr;
+            return cuda_fail(p, e, "m list");
+        }
+    }
+    cudaError_t e = cudaMemcpy(p.d_mflag, flag.data(), sizeof(int) * flag.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(p, e, "m list");
+    p.n_mlist = n;
+    return SHT_OK;
 }
 
 sht_status sht_plan_live_steps(sht_plan_t plan, int64_t *live, int64_t *total)
@@ -677,6 +721,10 @@ sht_status sht_map2alm(sht_plan_t plan, const double *map, void *alm, int nmaps,
 // Spin-2 transforms (see the header and spin.cu).
 static sht_status spin_prepare(Plan &p, int spin)
 {
+    if (p.n_mlist > 0) {
+        p.last_error = "an m list is set: the spin transforms compute every m";
+        return SHT_EUNSUPPORTED;
+    }
     if (spin != 2) {
         p.last_error = "spin-weighted transforms: only spin 2 is implemented";
         return SHT_EUNSUPPORTED;

@@ -37,6 +37,7 @@ EXPORTS = (
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
     "sht_plan_set_tuning", "sht_plan_tuning", "sht_plan_selftest_timeout", "sht_alm2map_ws", "sht_map2alm_ws",
     "sht_plan_live_steps", "sht_alm2map_spin", "sht_map2alm_spin", "sht_spin_workspace_bytes",
+    "sht_plan_set_mlist",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
@@ -98,6 +99,7 @@ def load():
             "sht_alm2map_spin": (I, [P, I, P, P, I, P]),
             "sht_map2alm_spin": (I, [P, I, P, P, I, P]),
             "sht_spin_workspace_bytes": (S, [P, I]),
+            "sht_plan_set_mlist": (I, [P, P, I]),
             "sht_plan_device_status": (I, [P, P, I]),
             "sht_plan_reserve": (I, [P, I]),
             "sht_plan_set_tuning": (I, [P, I, I]),
@@ -235,6 +237,12 @@ class Plan:
         if st != SHT_ETIMEOUT:
             _check(st, self._h)
         return int(v.value)
+
+    def set_mlist(self, ms=None):
+        """Restrict the FP64 Legendre steps to the listed m (None or empty: every m)."""
+        arr = np.ascontiguousarray([] if ms is None else ms, dtype=np.int32)
+        ptr = _np_ptr(arr) if arr.size else None
+        _check(load().sht_plan_set_mlist(self._h, ptr, int(arr.size)), self._h, "sht_plan_set_mlist")
 
     def live_steps(self):
         """(live, total) recurrence steps of one pass: total = nalm * slots; live from the first
