@@ -65,8 +65,7 @@ def parse():
     ap.add_argument("--mode", default="split", choices=["split", "fp64"],
                     help="split: tensor-core synthesis + double-float analysis (<= 1e-9); fp64: plain")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests in the serving trace (0: no serving leg)")
-    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate of the serving trace, 1/s")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
     ap.add_argument("--no-c2", dest="c2", action="store_false",
                     help="skip the plain FP64 lmax = 2048 leg (HEALPix 1024 and the Gauss-Legendre round trip)")
@@ -708,10 +707,11 @@ def o1_leg(lmax=64, nside=32):
 
 def batch_leg(a, rep, local_rank):
     """The batched form: `--batch-maps` maps, each with lmax drawn from {512, 1024, 2048} (HEALPix
-    nside = lmax/2) and alm2map or map2alm with probability 1/2, grouped into one call per
-    (lmax, direction) and run as one CUDA graph, plain FP64 and precision form side by side.
-    The knobs of every call are autotuned first (not timed); the graph replay and the same calls
-    made eagerly are timed with CUDA events, `--steps` times each after one warm-up."""
+    nside = lmax/2) and alm2map or map2alm with probability 1/2.  Plain FP64: one persistent launch
+    per stage and direction (tiles of all plans from one longest-first queue; the two directions on
+    two streams of one CUDA graph), batch knobs autotuned first.  Beside it, and for the precision
+    form, a CUDA graph of one library call per (lmax, direction) with the per-call knobs autotuned.
+    Replays and eager calls are timed with CUDA events, `--steps` times each after one warm-up."""
     import functools
 
     import numpy as np
@@ -775,98 +775,133 @@ def batch_leg(a, rep, local_rank):
             for st in b.streams:
                 stream.wait_stream(st)
 
-        def graph():
-            b.replay()
-
-        g_ms = timed(graph)
+        g_ms = timed(b.replay)
         e_ms = timed(eager)
-        status = max(p.device_status() for p in plans.values())
-        out[name] = {"graph_ms": g_ms, "maps_per_s": a.batch_maps / (g_ms * 1e-3),
-                     "eager_ms": e_ms, "eager_maps_per_s": a.batch_maps / (e_ms * 1e-3),
-                     "tune_s": tune_s, "capture_s": capture_s, "device_status": status,
-                     "tuned": {"%s lmax=%d" % (j.direction, j.plan.lmax): {"knobs": r["knobs"], "ms": r["ms"],
-                                                                          "default_ms": r["default_ms"]}
-                               for j, r in zip(jobs, recs)}}
-        del b, jobs
+        res = {"graph_of_calls_ms": g_ms, "graph_of_calls_maps_per_s": a.batch_maps / (g_ms * 1e-3),
+               "eager_ms": e_ms, "eager_maps_per_s": a.batch_maps / (e_ms * 1e-3),
+               "tune_s": tune_s, "capture_s": capture_s,
+               "tuned": {"%s lmax=%d" % (j.direction, j.plan.lmax): {"knobs": r["knobs"], "ms": r["ms"],
+                                                                    "default_ms": r["default_ms"]}
+                         for j, r in zip(jobs, recs)}}
+        del b
+        if mode == sht.MODE_FP64:
+            # the persistent form: one launch per stage and direction, tiles of every plan from one
+            # queue, longest first; the batch knobs (tile shapes, persistent grids) tuned first
+            pb = batch.PersistentBatch(jobs)
+            t0 = time.perf_counter()
+            cache = {}
+            ptuned = {d: autotune.tune_batch(bb, d, cache=cache, key=autotune.batch_key(
+                [(j.plan, j.src) for j in jobs if j.direction == d], d)) for d, bb in pb.batches}
+            ptune_s = time.perf_counter() - t0
+            pb.capture()
+            p_ms = timed(pb.replay)
+            res.update({"persistent_ms": p_ms, "maps_per_s": a.batch_maps / (p_ms * 1e-3), "persistent_tune_s": ptune_s,
+                        "persistent_tuned": {d: {"knobs": r["knobs"], "ms": r["ms"], "default_ms": r["default_ms"]}
+                                             for d, r in ptuned.items()},
+                        "tiles": {d: {"legendre": bb.tiles(0), "ring": bb.tiles(1)} for d, bb in pb.batches},
+                        "form": "persistent: one launch per stage and direction, longest-first tile queue, both "
+                                "directions on two streams of one CUDA graph"})
+            pb.close()
+        else:
+            res.update({"maps_per_s": res["graph_of_calls_maps_per_s"],
+                        "form": "graph of calls: one library call per (lmax, direction) on 2 streams of one CUDA "
+                                "graph (the tensor-core kernels have no persistent multi-plan form)"})
+        res["device_status"] = max(p.device_status() for p in plans.values())
+        out[name] = res
+        del jobs
         for p in plans.values():
             p.close()
         torch.cuda.empty_cache()
     out["precision_over_fp64"] = out["precision"]["maps_per_s"] / out["fp64"]["maps_per_s"]
-    out["form"] = ("one CUDA graph per batch: one library call per (lmax, direction), plans spread over 2 "
-                   "streams; knobs: maps or ring slots per launch, autotuned per call")
+    out["persistent_over_graph_of_calls_fp64"] = out["fp64"]["maps_per_s"] / out["fp64"]["graph_of_calls_maps_per_s"]
     return out
 
 
+def serve_grid():
+    """The serving trace's band limits: 16 values log-uniform between 256 and 4096, rounded to even
+    (nside = lmax / 2), most of them not powers of two."""
+    return [2 * int(round(128 * 16 ** (k / 15))) for k in range(16)]
+
+
 def serve_leg(a, rep, local_rank):
-    """A Poisson trace of alm2map / map2alm requests (lmax log-uniform over {256, ..., 4096} on
-    HEALPix nside = lmax/2, 1-32 maps each, C_l-shaped Gaussian a_lm or unit white-noise maps,
-    inputs resident on the device before their arrival), served twice: by the continuous-batching
-    server in the precision form on two streams, and by the plain FP64 path one request per call
-    in arrival order.  Latency = completion - arrival; maps/s = maps / (last completion - first
-    arrival)."""
+    """The serving trace of the benchmark's configuration 5: `--serve-requests` requests, lmax drawn
+    uniformly from serve_grid() (log-uniform over [256, 4096]) on HEALPix nside = lmax/2, 1-32 maps
+    each, alm2map or map2alm with probability 1/2, inputs a C_l-shaped Gaussian a_lm or unit white
+    noise, resident on the device before they arrive (one 32-map input per grid and direction,
+    requests take its first maps).  Served twice: by the continuous-batching server in the precision
+    form on two streams, and by the plain FP64 path one request per call in arrival order.  First
+    both at saturation (every request at t = 0: capacity, maps/s), then both under Poisson arrivals
+    at 80 % of the plain path's measured capacity (p50/p99 latency = completion - arrival)."""
     import numpy as np
     import torch
 
     from paper_1106_0159_gb300 import inputs, serve, sht
 
     g = np.random.Generator(np.random.PCG64(rep.seed(4242)))
-    lmaxes = [256, 512, 1024, 2048, 4096]
+    grid = serve_grid()
     spec = []
     for _ in range(a.serve_requests):
-        L = lmaxes[int(g.integers(len(lmaxes)))]
+        L = grid[int(g.integers(len(grid)))]
         spec.append((serve.ALM2MAP if g.random() < 0.5 else serve.MAP2ALM, L, L // 2, int(g.integers(1, 33))))
-    offsets = [t for t, _ in serve.poisson_trace(a.serve_rate, len(spec), lambda i: i, seed=rep.seed(4244))]
     gen = torch.Generator(device="cuda")
     gen.manual_seed(rep.seed(4243))
-    sds, datas = {}, []
+    pools = {}
     for d, L, ns, n in spec:
+        if (d, L) in pools:
+            continue
         if d == serve.ALM2MAP:
-            if L not in sds:
-                l, m = inputs.lm_arrays(L, L)
-                cl = 1.0 / (l * (l + 1.0) + 1.0)
-                sds[L] = (torch.from_numpy(np.where(m == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda(),
-                          torch.from_numpy(m != 0).cuda())
-            sd, mnz = sds[L]
-            re = torch.randn((n, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd
-            im = torch.randn((n, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd * mnz
-            datas.append(torch.complex(re, im))
+            l, m = inputs.lm_arrays(L, L)
+            cl = 1.0 / (l * (l + 1.0) + 1.0)
+            sd = torch.from_numpy(np.where(m == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda()
+            mnz = torch.from_numpy(m != 0).cuda()
+            re = torch.randn((32, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd
+            im = torch.randn((32, sd.numel()), dtype=torch.float64, device="cuda", generator=gen) * sd * mnz
+            pools[(d, L)] = torch.complex(re, im)
         else:
-            datas.append(torch.randn((n, 12 * ns * ns), dtype=torch.float64, device="cuda", generator=gen))
+            pools[(d, L)] = torch.randn((32, 12 * (L // 2) ** 2), dtype=torch.float64, device="cuda", generator=gen)
+    datas = [pools[(d, L)][:n] for d, L, ns, n in spec]
     torch.cuda.synchronize()
     keys = sorted(set((ns, L) for _, L, ns, _ in spec))
+    nmaps = sum(n for *_, n in spec)
+    mean_maps = nmaps / max(len(spec), 1)
 
-    def run(mode, nstreams, batching):
+    def run(mode, nstreams, batching, offsets, label):
         be = serve.TorchBackend(mode=mode, nstreams=nstreams, budget_fraction=0.8)
         warm_s = be.warm(keys, max_maps=32)
-        out = {"plan_warm_s": warm_s, "streams": nstreams, "batching": batching}
-        for name, offs in (("open_loop", offsets), ("saturated", [0.0] * len(spec))):
-            srv = serve.Server(be, max_batch_maps=32, nstreams=nstreams, batching=batching)
-            trace = [(t, serve.Request(d, L, ns, x, n)) for t, (d, L, ns, n), x in zip(offs, spec, datas)]
-            rep.barrier()
-            clocks = ClockSampler(local_rank)
-            clocks.start()
-            srv.run_trace(trace, timeout=600)
-            torch.cuda.synchronize()
-            st = srv.stats()
-            st["clocks"] = clocks.stop()
-            out[name] = st
-        out["device_status"] = max(be.plan(k).device_status() for k in keys)
+        srv = serve.Server(be, max_batch_maps=32, nstreams=nstreams, batching=batching, keep_results=False)
+        trace = [(t, serve.Request(d, L, ns, x, n)) for t, (d, L, ns, n), x in zip(offsets, spec, datas)]
+        rep.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        srv.run_trace(trace, timeout=1200)
+        torch.cuda.synchronize()
+        st = srv.stats()
+        st["clocks"] = clocks.stop()
+        st["plan_warm_s"] = warm_s
+        st["device_status"] = max(be.plan(k).device_status() for k in keys)
+        st["run"] = label
         be.close()
-        return out
+        return st
 
-    served = run(sht.MODE_SPLIT_BF16, 2, True)
-    plain = run(sht.MODE_FP64, 1, False)
-    del datas
+    zero = [0.0] * len(spec)
+    plain_sat = run(sht.MODE_FP64, 1, False, zero, "plain, saturated")
+    served_sat = run(sht.MODE_SPLIT_BF16, 2, True, zero, "served, saturated")
+    rate = 0.8 * plain_sat["maps_per_s"] / mean_maps   # requests per second
+    offsets = [t for t, _ in serve.poisson_trace(rate, len(spec), lambda i: i, seed=rep.seed(4244))]
+    plain_ol = run(sht.MODE_FP64, 1, False, offsets, "plain, Poisson at 80 % of plain capacity")
+    served_ol = run(sht.MODE_SPLIT_BF16, 2, True, offsets, "served, Poisson at 80 % of plain capacity")
+    del datas, pools
     torch.cuda.empty_cache()
-    nmaps = sum(n for *_, n in spec)
-    return {"trace": "%d requests, lmax log-uniform over %s (HEALPix nside = lmax/2), 1-32 maps each (%d maps), "
-                     "alm2map or map2alm with probability 1/2; inputs resident on the device. open_loop: Poisson "
-                     "arrivals at %.2f/s; saturated: all requests arrive at t = 0 (capacity)"
-                     % (len(spec), lmaxes, nmaps, a.serve_rate),
-            "served": served, "plain": plain,
-            "maps_per_s": {"served": served["saturated"]["maps_per_s"], "plain": plain["saturated"]["maps_per_s"]},
-            "p99_ms": {"served": served["open_loop"]["p99_ms"], "plain": plain["open_loop"]["p99_ms"]},
-            "served_over_plain_maps_per_s": served["saturated"]["maps_per_s"] / plain["saturated"]["maps_per_s"],
+    return {"trace": "%d requests (%d maps), lmax uniform over %s (log-uniform in [256, 4096], even; HEALPix "
+                     "nside = lmax/2), 1-32 maps each, alm2map or map2alm with probability 1/2; inputs resident "
+                     "on the device" % (len(spec), nmaps, grid),
+            "offered_rate_per_s": rate, "offered_load": "80 % of the plain path's saturated capacity",
+            "served": {"saturated": served_sat, "open_loop": served_ol},
+            "plain": {"saturated": plain_sat, "open_loop": plain_ol},
+            "maps_per_s": {"served": served_sat["maps_per_s"], "plain": plain_sat["maps_per_s"]},
+            "p50_ms": {"served": served_ol["p50_ms"], "plain": plain_ol["p50_ms"]},
+            "p99_ms": {"served": served_ol["p99_ms"], "plain": plain_ol["p99_ms"]},
+            "served_over_plain_maps_per_s": served_sat["maps_per_s"] / plain_sat["maps_per_s"],
             "served_form": "continuous batching, up to 32 maps of one plan and direction per call, 2 streams, "
                            "precision form",
             "plain_form": "one request per call in arrival order, 1 stream, plain FP64"}

@@ -246,6 +246,41 @@ sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value);
 int sht_plan_tuning(sht_plan_t plan, int knob); /* the knob's value; -1 for a null plan or unknown knob */
 
 /*
+ * Batched form (no counterpart in the paper, which runs one transform at a time): many transforms
+ * of one direction over plans of uneven lmax run as one persistent launch per stage.  The CTAs of a
+ * launch take work tiles from a device queue in the order the host sorted them, longest first:
+ * for the Legendre steps a tile is (transform, group of maps, m, block of ring slots), ordered by
+ * its l-range times its maps (the min-max pairing of Section 4.2.1 turned into a queue); for the
+ * ring steps a unit is (transform, ring pair, map), ordered by DFT length.  alm2map: Legendre
+ * synthesis then ring synthesis; map2alm: ring analysis, Legendre analysis and the fixed-order
+ * block reduction.  Job j is plans[j] on in[j] -> out[j] with nmaps[j] maps (device buffers in the
+ * layouts of sht_alm2map / sht_map2alm; the batch keeps the pointers: write new inputs in place
+ * between runs).  All plans must be in SHT_MODE_FP64 without an m list (SHT_EUNSUPPORTED
+ * otherwise); the plans must outlive the batch.  The batch owns its Delta slabs, partial sums,
+ * ring scratch and queue counters (allocated at creation, and again when a knob changes).
+ * sht_batch_run enqueues only stream work on `stream` (a memset of the counters and the
+ * launches), so it can be captured in a CUDA graph.  Results equal the one-plan calls bit for bit
+ * (same kernels, same summation order), whatever the knobs.
+ */
+typedef struct sht_batch_s *sht_batch_t;
+typedef enum {
+    SHT_BATCH_SYNTH_MAPS = 0,  /* maps per Legendre synthesis tile: 1, 2 or 4 (default 4) */
+    SHT_BATCH_LEG_CTAS = 1,    /* persistent Legendre CTAs per SM: 2, 4, 8 or 16 (default 8) */
+    SHT_BATCH_RING_CTAS = 2,   /* persistent ring CTAs per SM: 1 to 4 (default 4) */
+    SHT_BATCH_ANAL_MAPS = 3,   /* maps per Legendre analysis tile: 1 or 2 (default 2) */
+    SHT_BATCH_ANAL_SLOTS = 4,  /* ring slots per thread of the analysis tiles: 1 or 4 (default 1) */
+    SHT_BATCH_TUNE_COUNT = 5
+} sht_batch_tune;
+sht_status  sht_batch_create(sht_batch_t *out, int direction /* 0 alm2map, 1 map2alm */, int njobs,
+                             const sht_plan_t *plans, const void *const *in, void *const *outs, const int *nmaps);
+sht_status  sht_batch_set_tuning(sht_batch_t batch, int knob, int value); /* host call; rebuilds tiles and scratch */
+int         sht_batch_tuning(sht_batch_t batch, int knob);
+sht_status  sht_batch_run(sht_batch_t batch, void *stream);
+int64_t     sht_batch_tiles(sht_batch_t batch, int stage); /* 0: Legendre tiles, 1: ring units; -1 if invalid */
+const char *sht_batch_last_error(sht_batch_t batch);
+void        sht_batch_destroy(sht_batch_t batch);          /* synchronises the device; NULL is ignored */
+
+/*
  * Grid helpers (pure host).  HEALPix (Gorski et al. 2005, the grid of
  * Section 5): 4 nside - 1 rings north to south, caller arrays of that length,
  * equal weights 4 pi / (12 nside^2).  Gauss-Legendre: nrings rings at the
@@ -309,6 +344,15 @@ sht_status sht_fp64_fma_tflops(double *tflops);
  */
 sht_status sht_alm2map_noalloc(sht_plan_t plan, const void *alm, double *map, int nmaps, void *stream);
 size_t     sht_noalloc_scratch_bytes(void);
+
+/*
+ * Host-side fault injection for tests (no counterpart in the paper): after n more successful device
+ * allocations, the library's next allocation fails as if the device were out of memory (the call
+ * returns cudaErrorMemoryAllocation internally, so the public call returns SHT_ENOMEM), and every
+ * later one too, until the injector is switched off with a negative n.  Process-wide; returns the
+ * previous setting.  Lets a test check that every allocation failure leaves nothing allocated.
+ */
+long sht_debug_fail_allocations_after(long n);
 
 const char *sht_status_string(sht_status s);
 const char *sht_plan_last_error(sht_plan_t plan);     /* "" when none */

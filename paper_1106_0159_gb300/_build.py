@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsht.so")
-SOURCES = ["sht_plan.cu", "legendre.cu", "legendre_tc.cu", "legendre_df.cu", "ringfft.cu", "diag.cu", "noalloc.cu", "spin.cu"]
+SOURCES = ["sht_plan.cu", "legendre.cu", "legendre_tc.cu", "legendre_df.cu", "ringfft.cu", "diag.cu", "noalloc.cu", "spin.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

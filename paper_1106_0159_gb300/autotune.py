@@ -129,3 +129,68 @@ class Autotuner:
         self.cache[key] = rec
         self._save()
         return rec
+
+
+# ---------------------------------------------------------------- the persistent batched form
+
+def batch_knobs(direction: str) -> List[int]:
+    """The batch knobs a direction reads: tile shapes (maps per tile, slots per thread) and the
+    persistent grids (CTAs per SM of the Legendre and ring launches)."""
+    if direction == ALM2MAP:
+        return [sht.BATCH_SYNTH_MAPS, sht.BATCH_LEG_CTAS, sht.BATCH_RING_CTAS]
+    if direction == MAP2ALM:
+        return [sht.BATCH_ANAL_MAPS, sht.BATCH_ANAL_SLOTS, sht.BATCH_LEG_CTAS, sht.BATCH_RING_CTAS]
+    raise ValueError("unknown direction %r" % (direction,))
+
+
+def batch_key(jobs, direction: str) -> str:
+    """Cache key of a batch: its (grid size, lmax, maps) jobs, the mode and the direction."""
+    parts = sorted("%d:%d:%d:%d" % (j[0].npix, j[0].lmax, j[0].mode, int(j[1].shape[0])) for j in jobs)
+    return "batch %s %s" % (direction, ",".join(parts))
+
+
+def batch_timer(batch, reps: int = 2) -> float:
+    """Milliseconds of one batch run (median of `reps` after one warm-up), CUDA events."""
+    import torch
+    batch.run()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.run()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def tune_batch(batch, direction: str, timer: Callable = batch_timer, cache: Optional[Dict[str, dict]] = None,
+               key: Optional[str] = None) -> dict:
+    """Coordinate search over the batch knobs: from the defaults, each knob in turn takes the
+    fastest of its values with the others fixed, twice over.  Returns {"knobs", "ms", "default_ms",
+    "tried"}; with a cache and a key, a cached record is applied without timing."""
+    if cache is not None and key is not None and key in cache:
+        for k, v in cache[key]["knobs"].items():
+            batch.set_tuning(int(k), int(v))
+        return cache[key]
+    ks = batch_knobs(direction)
+    cur = {k: batch.tuning(k) for k in ks}
+    default_ms = float(timer(batch))
+    best_ms = default_ms
+    tried = []
+    for _ in range(2):
+        for k in ks:
+            for v in sht.BATCH_TUNE_VALUES[k]:
+                if v == cur[k]:
+                    continue
+                batch.set_tuning(k, v)
+                t = float(timer(batch))
+                tried.append([{str(kk): (v if kk == k else cur[kk]) for kk in ks}, t])
+                if t < best_ms:
+                    best_ms, cur[k] = t, v
+                batch.set_tuning(k, cur[k])
+    rec = {"knobs": {str(k): v for k, v in cur.items()}, "ms": best_ms, "default_ms": default_ms, "tried": tried}
+    if cache is not None and key is not None:
+        cache[key] = rec
+    return rec

@@ -1,6 +1,13 @@
 """A fixed batch of transforms (several plans, band limits, directions and map counts) run as
 one CUDA graph.
 
+Two forms.  PersistentBatch (plain FP64 plans): every transform of one direction is one library
+batch (sht_batch_*): one persistent launch per stage whose CTAs take (transform, map group, m,
+slot block) tiles of all plans from one device queue, longest l-range first, and (transform, ring
+pair, map) DFT units longest first; the alm2map batch and the map2alm batch run on two streams
+inside one graph, so the ring stage of one direction overlaps the Legendre stage of the other.
+GraphBatch (any mode): one library call per job, as below.
+
 Each job is one library call (sht_alm2map or sht_map2alm) with device buffers that stay put.
 Jobs of one plan run in order on one stream (a plan's scratch serves one stream); the plans are
 spread over a few streams that fork from and join the capture stream, so independent plans
@@ -106,3 +113,57 @@ class GraphBatch:
         if self.graph is None:
             raise RuntimeError("capture() first")
         self.graph.replay()
+
+
+class PersistentBatch:
+    """All jobs of one direction in one sht batch (plain FP64 plans); the two directions on two
+    streams of one CUDA graph.  Same interface as GraphBatch."""
+
+    def __init__(self, jobs: List[Job], nstreams: int = 2):
+        from . import sht
+        self.jobs = list(jobs)
+        self.batches = []
+        for d, code in ((ALM2MAP, sht.BATCH_ALM2MAP), (MAP2ALM, sht.BATCH_MAP2ALM)):
+            js = [j for j in self.jobs if j.direction == d]
+            if js:
+                self.batches.append((d, sht.Batch(code, [(j.plan, j.src, j.dst) for j in js])))
+        for j in self.jobs:
+            if j.direction not in (ALM2MAP, MAP2ALM):
+                raise ValueError("unknown direction %r" % (j.direction,))
+        self.nstreams = max(1, min(nstreams, len(self.batches)))
+        self.graph = None
+        self.streams = None
+
+    def run_eager(self, streams=None):
+        import torch
+        cur = torch.cuda.current_stream()
+        for i, (_, b) in enumerate(self.batches):
+            st = streams[i % len(streams)] if streams else cur
+            b.run(stream=st)
+
+    def capture(self):
+        import torch
+        self.run_eager()
+        torch.cuda.synchronize()
+        self.streams = [torch.cuda.Stream() for _ in range(self.nstreams)]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.streams[0]):
+            s0 = self.streams[0]
+            for st in self.streams[1:]:
+                st.wait_stream(s0)
+            for i, (_, b) in enumerate(self.batches):
+                b.run(stream=self.streams[i % self.nstreams])
+            for st in self.streams[1:]:
+                s0.wait_stream(st)
+        self.graph = g
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    def close(self):
+        for _, b in self.batches:
+            b.close()
+        self.batches = []

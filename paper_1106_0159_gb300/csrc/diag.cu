@@ -68,7 +68,7 @@ extern "C" sht_status sht_fp64_fma_tflops(double *tflops)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SHT_ECUDA;
     const int blocks = sms * 8;
     double *out = nullptr;
-    if (cudaMalloc(&out, sizeof(double) * blocks * DIAG_T) != cudaSuccess) return SHT_ENOMEM;
+    if (sht::dev_malloc(&out, sizeof(double) * blocks * DIAG_T) != cudaSuccess) return SHT_ENOMEM;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -47,6 +47,7 @@
 #include "sht_internal.h"
 
 #include <algorithm>
+#include <vector>
 
 namespace sht {
 namespace {
@@ -480,6 +481,99 @@ __global__ void reduce_blocks_kernel(const double2 *__restrict__ partial, const 
     }
 }
 
+// ---------------------------------------------------------------- batched form (many plans)
+//
+// One persistent launch runs the Legendre tiles of many transforms (uneven lmax, any number of
+// maps each): a tile is (job, first map, maps, m, slot block), the host sorts the tiles by their
+// l-range, longest first (the min-max balancing of the paper's Section 4.2.1 carried over to a
+// queue), and every CTA takes the next tile from a device counter until the queue is empty.
+
+// tile: x = job, y = m, z = slot block, w = first map | (maps << 16)
+__global__ void __launch_bounds__(SYN_T) legendre_synth_batch_kernel(const SynArgs *__restrict__ jobs,
+                                                                     const int4 *__restrict__ tiles, int ntiles,
+                                                                     int *counter)
+{
+    __shared__ Coef C;
+    __shared__ double2 s_a[4][CHL];
+    __shared__ int s_t;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_t;
+        if (t >= ntiles) break;
+        const int4 T = tiles[t];
+        SynArgs A = jobs[T.x];
+        const int g0 = T.w & 0xffff, nm = T.w >> 16;
+        A.alm += (int64_t)g0 * A.nalm;
+        A.delta += (int64_t)g0 * A.nrings * (A.mmax + 1);
+        const int m = T.y, blk = T.z;
+        const bool polar = m <= A.mR && A.s[blk * SYN_T] < POLAR_SIN;
+        if (nm == 4) {
+            if (polar) synth_body<4, true>(A, m, blk, C, s_a); else synth_body<4, false>(A, m, blk, C, s_a);
+        } else if (nm == 2) {
+            if (polar) synth_body<2, true>(A, m, blk, C, s_a); else synth_body<2, false>(A, m, blk, C, s_a);
+        } else {
+            if (polar) synth_body<1, true>(A, m, blk, C, s_a); else synth_body<1, false>(A, m, blk, C, s_a);
+        }
+    }
+}
+
+// tile: x = job, y = m, z = slot block (K * 128 slots), w = first map | (maps << 16); the partial
+// sums of job j go to its own buffer (A.partial), reduced afterwards by reduce_blocks_batch_kernel
+template <int K>
+__global__ void __launch_bounds__(ANA_T) legendre_anal_batch_kernel(const AnaArgs *__restrict__ jobs,
+                                                                    const int4 *__restrict__ tiles, int ntiles,
+                                                                    int *counter)
+{
+    constexpr int NW = ANA_T / 32;
+    __shared__ Coef C;
+    __shared__ double s_red_raw[NW * CHL * 4];
+    __shared__ int s_t;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_t;
+        if (t >= ntiles) break;
+        const int4 T = tiles[t];
+        AnaArgs A = jobs[T.x];
+        const int g0 = T.w & 0xffff, nm = T.w >> 16;
+        A.delta += (int64_t)g0 * A.nrings * (A.mmax + 1);
+        A.partial += (int64_t)g0 * A.part_map_stride;
+        const int m = T.y, blk = T.z;
+        const bool polar = m <= A.mR && A.s[blk * (ANA_T * K)] < POLAR_SIN;
+        if (nm == 2) {
+            auto *r = reinterpret_cast<double(*)[CHL][4]>(s_red_raw);
+            if (polar) anal_body<2, K, true>(A, m, blk, C, r); else anal_body<2, K, false>(A, m, blk, C, r);
+        } else {
+            auto *r = reinterpret_cast<double(*)[CHL][2]>(s_red_raw);
+            if (polar) anal_body<1, K, true>(A, m, blk, C, r); else anal_body<1, K, false>(A, m, blk, C, r);
+        }
+    }
+}
+
+// a_lm = c_lm * sum over ring blocks, for every job of the batch (one launch)
+__global__ void reduce_blocks_batch_kernel(const BatchReduceJob *__restrict__ jobs, int njobs)
+{
+    for (int j = 0; j < njobs; ++j) {
+        const BatchReduceJob J = jobs[j];
+        const int64_t total = J.nalm * J.nmaps;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t g = t / J.nalm, i = t - g * J.nalm;
+            double re = 0.0, im = 0.0;
+            for (int b = 0; b < J.nblk; ++b) {
+                const double2 v = J.partial[b * J.blk_stride + g * J.nalm + i];
+                re += v.x;
+                im += v.y;
+            }
+            const double c = J.cfac[i];
+            J.alm[t] = make_double2(c * re, i <= J.lmax ? 0.0 : c * im);
+        }
+    }
+}
+
 int anal_slots_per_cta(const Plan &p) { return p.tune[SHT_TUNE_ANAL_SLOTS] * ANA_T; }
 
 }  // namespace
@@ -592,6 +686,152 @@ cudaError_t launch_legendre_anal(const Plan &p, const double2 *delta, double2 *p
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- batched form: host side
+
+namespace {
+template <class T>
+cudaError_t upload_vec(T **dst, const std::vector<T> &v)
+{
+    cudaError_t e = dev_malloc(dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// tiles of every job, each job's maps cut into groups of at most `most`, sorted by l-range x maps
+// (longest first; ties: lower job first)
+std::vector<int4> batch_tiles(const std::vector<const Plan *> &plans, const std::vector<int> &nmaps, int most,
+                              int slots_per_cta)
+{
+    struct Key {
+        int64_t cost;
+        int4 t;
+    };
+    std::vector<Key> keys;
+    for (size_t j = 0; j < plans.size(); ++j) {
+        const Plan &p = *plans[j];
+        const int nblk = (p.nslots + slots_per_cta - 1) / slots_per_cta;
+        for (int g0 = 0; g0 < nmaps[j]; g0 += most) {
+            const int nm = std::min(most, nmaps[j] - g0);
+            const int nmq = nm >= 4 ? 4 : nm >= 2 ? 2 : 1;  // the kernels take 4, 2 or 1 maps
+            for (int g = g0; g < g0 + nm; g += nmq) {
+                const int n = std::min(nmq, g0 + nm - g);
+                const int q = n >= 4 ? 4 : n >= 2 ? 2 : 1;
+                for (int m = 0; m <= p.mmax; ++m)
+                    for (int b = 0; b < nblk; ++b)
+                        keys.push_back({(int64_t)(p.lmax - m + 1) * q, make_int4((int)j, m, b, g | (q << 16))});
+            }
+        }
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) { return a.cost > b.cost; });
+    std::vector<int4> out(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) out[i] = keys[i].t;
+    return out;
+}
+}  // namespace
+
+cudaError_t batch_legendre_synth_setup(const std::vector<const Plan *> &plans, const std::vector<const double2 *> &alm,
+                                       const std::vector<double2 *> &delta, const std::vector<int> &nmaps,
+                                       int maps_per_tile, BatchLaunch &L)
+{
+    std::vector<SynArgs> jobs(plans.size());
+    for (size_t j = 0; j < plans.size(); ++j) {
+        const Plan &p = *plans[j];
+        SynArgs &A = jobs[j];
+        A = SynArgs{};
+        A.alm = alm[j];
+        A.delta = delta[j];
+        A.slotN = p.d_slotN;
+        A.slotS = p.d_slotS;
+        A.u = p.d_u;
+        A.s = p.d_s;
+        A.alpha = p.d_alpha;
+        A.cfac = p.d_cfac;
+        A.rein = p.d_rein;
+        A.mflag = nullptr;
+        A.mR = p.mR;
+        A.nslots = p.nslots;
+        A.nblk = (p.nslots + SYN_T - 1) / SYN_T;
+        A.lmax = p.lmax;
+        A.mmax = p.mmax;
+        A.nrings = p.nrings;
+        A.nalm = p.nalm;
+    }
+    const std::vector<int4> tiles = batch_tiles(plans, nmaps, maps_per_tile, SYN_T);
+    L.ntiles = (int)tiles.size();
+    cudaError_t e = upload_vec((SynArgs **)&L.jobs, jobs);
+    if (e == cudaSuccess) e = upload_vec(&L.tiles, tiles);
+    return e;
+}
+
+cudaError_t batch_legendre_anal_setup(const std::vector<const Plan *> &plans, const std::vector<const double2 *> &delta,
+                                      const std::vector<double2 *> &partial, const std::vector<double2 *> &alm,
+                                      const std::vector<int> &nmaps, int maps_per_tile, int slots_per_thread,
+                                      BatchLaunch &L, BatchLaunch &R)
+{
+    const int per = slots_per_thread * ANA_T;
+    std::vector<AnaArgs> jobs(plans.size());
+    std::vector<BatchReduceJob> red(plans.size());
+    for (size_t j = 0; j < plans.size(); ++j) {
+        const Plan &p = *plans[j];
+        AnaArgs &A = jobs[j];
+        A = AnaArgs{};
+        A.delta = delta[j];
+        A.partial = partial[j];
+        A.slotN = p.d_slotN;
+        A.slotS = p.d_slotS;
+        A.u = p.d_u;
+        A.s = p.d_s;
+        A.alpha = p.d_alpha;
+        A.cfac = p.d_cfac;
+        A.rein = p.d_rein;
+        A.mflag = nullptr;
+        A.mR = p.mR;
+        A.nslots = p.nslots;
+        A.nblk = (p.nslots + per - 1) / per;
+        A.lmax = p.lmax;
+        A.mmax = p.mmax;
+        A.nrings = p.nrings;
+        A.nalm = p.nalm;
+        A.part_map_stride = p.nalm;
+        A.part_blk_stride = (int64_t)nmaps[j] * p.nalm;
+        red[j] = BatchReduceJob{partial[j], p.d_cfac, alm[j], A.nblk, p.nalm, nmaps[j], p.lmax,
+                                (int64_t)nmaps[j] * p.nalm};
+    }
+    const std::vector<int4> tiles = batch_tiles(plans, nmaps, std::min(maps_per_tile, 2), per);
+    L.ntiles = (int)tiles.size();
+    L.k = slots_per_thread;
+    R.ntiles = (int)plans.size();
+    cudaError_t e = upload_vec((AnaArgs **)&L.jobs, jobs);
+    if (e == cudaSuccess) e = upload_vec(&L.tiles, tiles);
+    if (e == cudaSuccess) e = upload_vec((BatchReduceJob **)&R.jobs, red);
+    return e;
+}
+
+size_t batch_anal_partial_bytes(const Plan &p, int nmaps, int slots_per_thread)
+{
+    const int per = slots_per_thread * ANA_T;
+    return (size_t)((p.nslots + per - 1) / per) * nmaps * (size_t)p.nalm * sizeof(double2);
+}
+
+cudaError_t batch_legendre_synth_launch(const BatchLaunch &L, int *counter, int grid, cudaStream_t st)
+{
+    legendre_synth_batch_kernel<<<grid, SYN_T, 0, st>>>((const SynArgs *)L.jobs, L.tiles, L.ntiles, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_legendre_anal_launch(const BatchLaunch &L, const BatchLaunch &R, int *counter, int grid,
+                                       cudaStream_t st)
+{
+    if (L.k == 4)
+        legendre_anal_batch_kernel<4><<<grid, ANA_T, 0, st>>>((const AnaArgs *)L.jobs, L.tiles, L.ntiles, counter);
+    else
+        legendre_anal_batch_kernel<1><<<grid, ANA_T, 0, st>>>((const AnaArgs *)L.jobs, L.tiles, L.ntiles, counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_blocks_batch_kernel<<<152 * 8, 256, 0, st>>>((const BatchReduceJob *)R.jobs, R.ntiles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *alm, int nmaps, cudaStream_t st)

@@ -293,20 +293,23 @@ __global__ void __launch_bounds__(DF_T) legendre_anal_df_kernel(DfArgs A)
 __global__ void reduce_blocks_df_kernel(const float4 *__restrict__ partial, const double2 *__restrict__ polar,
                                         int64_t polar_stride, int polar_blocks, const double *__restrict__ cfac,
                                         double2 *__restrict__ alm, int nblk, int64_t nalm, int nmaps, int lmax,
-                                        int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim)
+                                        int64_t blk_stride, int64_t map_stride, int64_t idx_stride, int64_t fp64_lim,
+                                        int64_t i0, int64_t nidx)
 {
-    const int64_t total = nalm * nmaps;
+    // coefficient indices i0 .. i0 + nidx - 1; the partial sums are indexed from i0
+    const int64_t total = nidx * nmaps;
     const bool maps_inner = map_stride < idx_stride;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t g, i;
+        int64_t g, il;
         if (maps_inner) {
-            i = t / nmaps;
-            g = t - i * nmaps;
+            il = t / nmaps;
+            g = t - il * nmaps;
         } else {
-            g = t / nalm;
-            i = t - g * nalm;
+            g = t / nidx;
+            il = t - g * nidx;
         }
-        const float4 *src = partial + g * map_stride + i * idx_stride;
+        const int64_t i = i0 + il;
+        const float4 *src = partial + g * map_stride + il * idx_stride;
         float2 re, im;
         int bk0 = 1;
         if (i < fp64_lim) {
@@ -481,12 +484,13 @@ DfArgs df_args(const Plan &p)
 cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
                                     int polar_blocks, const double *cfac, double2 *alm, int nblk, int64_t nalm,
                                     int nmaps, int lmax, int64_t blk_stride, int64_t map_stride, int64_t idx_stride,
-                                    int64_t fp64_lim, cudaStream_t st)
+                                    int64_t fp64_lim, cudaStream_t st, int64_t i0, int64_t nidx)
 {
-    const int64_t total = nalm * nmaps;
-    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (nidx < 0) nidx = nalm - i0;
+    const int64_t total = nidx * nmaps;
+    const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
     reduce_blocks_df_kernel<<<rgrid, 256, 0, st>>>(partial, polar, polar_stride, polar_blocks, cfac, alm, nblk, nalm,
-                                                   nmaps, lmax, blk_stride, map_stride, idx_stride, fp64_lim);
+                                                   nmaps, lmax, blk_stride, map_stride, idx_stride, fp64_lim, i0, nidx);
     return cudaGetLastError();
 }
 

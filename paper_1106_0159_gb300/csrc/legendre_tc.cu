@@ -224,6 +224,8 @@ struct TcArgs {
     int nslots, nblk, lmax, mmax, nrings, mR, nmaps;
     int polar_slots;         // analysis: slots the Reinsch-form kernel covers for m <= mR (mR < 0: none)
     int64_t nalm;
+    int m0;                  // analysis: first m of this launch (an m-slab)
+    int64_t idx0, nalm_part; // analysis: partial sums hold the indices idx0 .. idx0 + nalm_part - 1
 };
 
 // ---------------------------------------------------------------- a_lm side
@@ -486,16 +488,29 @@ __device__ __forceinline__ void recurrence_warps(const TcArgs &A, int m, int blk
         for (int h = 0; h < 2; ++h) {
             const bool scaled = __any_sync(0xffffffffu, k < 0);
             const bool drop = scaled && k < 0;
+            // Groups of 8 steps: the 8 factors alpha x = alpha (1 - u) first (they do not depend on y),
+            // then the chain of 8 dependent DFMAs, then the 8 stores.  Each step adds one DFMA to the
+            // dependency chain, and a warp issues in order: a store right after its y would hold the
+            // warp until y is ready and leave the FP64 pipe without the next factors to work on.
 #pragma unroll
-            for (int j = 16 * h; j < 16 * h + 16; ++j) {
-                // alpha x = alpha (1 - u) does not depend on y, so each step adds one DFMA
-                // (not two) to the dependency chain: one chain per SMSP is latency-bound
-                const double a = __shfl_sync(0xffffffffu, al_cur, j);
-                const double ax = fma(-a, u, a);
-                const double y = fma(ax, y1, -y2);
-                y2 = y1;
-                y1 = y;
-                if (q >= 0) yb[j * YS + r] = drop ? 0.0 : y;
+            for (int j0 = 16 * h; j0 < 16 * h + 16; j0 += 8) {
+                double ax[8], yv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const double a = __shfl_sync(0xffffffffu, al_cur, j0 + j);
+                    ax[j] = fma(-a, u, a);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const double y = fma(ax[j], y1, -y2);
+                    y2 = y1;
+                    y1 = y;
+                    yv[j] = y;
+                }
+                if (q >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) yb[(j0 + j) * YS + r] = drop ? 0.0 : yv[j];
+                }
             }
             if (drop && max(dexp(y1), dexp(y2)) > RESCALE_THR) {
                 y1 *= 0x1p-512;
@@ -770,15 +785,19 @@ constexpr int TA_XKB = TA_XD * (TA_R / 8) * 128;  // bytes between 8-slot groups
 constexpr int TA_BDIG = (TC_CH / 8) * 128;        // one digit of one 8-slot group of a K-step's y tile
 constexpr int TA_BKB = TA_XD * TA_BDIG;           // bytes between the two 8-slot groups of a y tile
 constexpr int TA_BTILE = 2 * TA_BKB;              // one K-step's y tile, [slot / 8][digit][l / 8] core matrices
+constexpr int TA_NB = 3;                          // y tile buffers (K-steps in flight between split and MMA)
 constexpr int TA_ACC = TA_REG * TA_N;             // tensor-memory columns of one chunk's accumulators
 constexpr int TA_OFF_B = TA_XBYTES;
-constexpr int TA_OFF_Y = TA_OFF_B + 2 * TA_BTILE;
+constexpr int TA_OFF_Y = TA_OFF_B + TA_NB * TA_BTILE;
 constexpr int TA_OFF_X = TA_OFF_Y + 2 * TC_CH * TA_YS * 8;
 constexpr int TA_OFF_E = TA_OFF_X + TA_R * 16 * 8;
 constexpr int TA_OFF_BAR = TA_OFF_E + TA_R * 4;
-constexpr int TA_SMEM = TA_OFF_BAR + 64 + 1024;   // + alignment slack
+constexpr int TA_NBAR = 2 * TA_NB + 4;            // done[NB], full[NB], tfree[2], afull[2]
+constexpr int TA_SMEM = TA_OFF_BAR + TA_NBAR * 8 + 16 + 128;
 constexpr int TA_TMEM_COLS = 512;                 // two chunks of accumulators
-constexpr int TA_NT = TC_NT + 32;                 // 4 recurrence + 8 split warps + 1 MMA-issuing warp
+constexpr int TA_NEPI = 4 * 32;                   // epilogue threads (one warp per tensor-memory lane quarter)
+constexpr int TA_NT = TC_NT + TA_NEPI + 32;       // 4 recurrence + 8 split + 4 epilogue warps + 1 MMA-issuing warp
+enum : int { BAR_EPI = 7, BAR_PREP = 8 };         // epilogue warps; split + epilogue warps after the X digits
 static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
 static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
 static_assert(TC_S == 7 && TA_XD == 8, "the digit stacks pair digits 0-1, 2-3, 4-5, 6-7");
@@ -798,35 +817,54 @@ __device__ __forceinline__ float2 df_sum(float2 a, float2 b)
     return make_float2(s.x, s.y + a.y + b.y);
 }
 
-// columns n0 .. n0 + 7 and 32 + n0 .. 32 + n0 + 7 (the two y-digit halves) of the 4 accumulator
-// regions of chunk buffer tb, this warp's lanes, summed as double-float pairs (classes roughly in
-// decreasing size); the eight loads are issued together and waited for once
-__device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int n0, float2 acc[8])
+// Columns 16 es .. 16 es + 15 (this row's parity) of both y-digit halves of the 4 accumulator
+// regions of chunk buffer tb, this warp's lanes, summed as double-float pairs in the order
+// (region 0 half 0, region 0 half 1, region 1 half 0, ...), classes roughly in decreasing size; the
+// loads go out four at a time and are waited for together.
+__device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int es, float2 acc[16])
 {
-    uint32_t v[2 * TA_REG][8];
 #pragma unroll
-    for (int h = 0; h < 2 * TA_REG; ++h) {
-        const int reg = h >> 1, half = h & 1;
-        const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) +
-                              (uint32_t)(tb * TA_ACC + reg * TA_N + half * TC_CH + n0);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[h][0]), "=r"(v[h][1]), "=r"(v[h][2]), "=r"(v[h][3]), "=r"(v[h][4]), "=r"(v[h][5]),
-                       "=r"(v[h][6]), "=r"(v[h][7])
-                     : "r"(addr));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int t = 0; t < 16; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = make_float2(0.f, 0.f);
+    for (int h0 = 0; h0 < 2 * TA_REG; h0 += 4) {
+        uint32_t v[4][16];
 #pragma unroll
-    for (int h = 0; h < 2 * TA_REG; ++h) {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const float2 sm = two_sum(acc[t].x, __uint_as_float(v[h][t]));
-            acc[t] = make_float2(sm.x, acc[t].y + sm.y);
+        for (int hh = 0; hh < 4; ++hh) {
+            const int h = h0 + hh, reg = h >> 1, half = h & 1;
+            const uint32_t addr = tmem + ((uint32_t)(32 * quarter) << 16) +
+                                  (uint32_t)(tb * TA_ACC + reg * TA_N + half * TC_CH + 16 * es);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[hh][0]), "=r"(v[hh][1]), "=r"(v[hh][2]), "=r"(v[hh][3]), "=r"(v[hh][4]), "=r"(v[hh][5]),
+                  "=r"(v[hh][6]), "=r"(v[hh][7]), "=r"(v[hh][8]), "=r"(v[hh][9]), "=r"(v[hh][10]), "=r"(v[hh][11]),
+                  "=r"(v[hh][12]), "=r"(v[hh][13]), "=r"(v[hh][14]), "=r"(v[hh][15])
+                : "r"(addr));
         }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const float2 sm = two_sum(acc[t].x, __uint_as_float(v[hh][t]));
+                acc[t] = make_float2(sm.x, acc[t].y + sm.y);
+            }
     }
 }
 
+// CTA: one m, 128 slots, 544 threads in five roles.
+//   warps 0-3   recurrence (recurrence_warps, double-buffered y stage of 32 l);
+//   warps 4-11  split: cut the X digits of the block once, then per K-step (16 slots) the y values
+//               into one of TA_NB y tiles, and arrive on its full barrier;
+//   warp 16     MMA issue: per K-step wait for the tile, issue its 10 MMAs, commit them to the
+//               tile's done barrier (the split waits on it before reusing the tile), and after the
+//               last K-step of a chunk also to the accumulator set's afull barrier;
+//   warps 12-15 epilogue, one per tensor-memory lane quarter: wait for afull, read the set, release
+//               it (tfree), add the bottom halves (lane quarters 2, 3) to the top ones (0, 1) through
+//               shared memory and write the block's partial a_lm / c_lm.
+// Every barrier phase a warp waits for can run at most one phase ahead of that wait, so the
+// parity tests are unambiguous; every mbarrier wait is bounded and the epilogue warps agree on
+// their outcome (bar.red) so that their named barriers stay balanced.
 __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -835,17 +873,19 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
     double *ybuf = (double *)(smem + TA_OFF_Y);             // [stage][32 l][TA_YS]
     float2 *xch = (float2 *)(smem + TA_OFF_X);              // [16 columns][64 rows] bottom-half sums
     int *sEx = (int *)(smem + TA_OFF_E);                    // [64] row exponents (biased, 0: all zero)
-    uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // done[2] (MMAs of a B buffer complete),
-    uint64_t *full = mbar + 2;                              // full[2] (a B buffer written),
-    uint64_t *tfree = mbar + 4;                             // tfree[2] (an accumulator set read out)
-    uint32_t *tslot = (uint32_t *)(mbar + 6);
+    uint64_t *mbar = (uint64_t *)(smem + TA_OFF_BAR);       // done[NB]: MMAs of a y tile complete
+    uint64_t *full = mbar + TA_NB;                          // full[NB]: a y tile written
+    uint64_t *tfree = full + TA_NB;                         // tfree[2]: an accumulator set read out
+    uint64_t *afull = tfree + 2;                            // afull[2]: an accumulator set complete
+    uint32_t *tslot = (uint32_t *)(afull + 2);
 
-    const int m = blockIdx.x / A.nblk;
-    const int blk = blockIdx.x - m * A.nblk;
+    const int m = A.m0 + (int)(blockIdx.x / A.nblk);
+    const int blk = (int)(blockIdx.x % A.nblk);
     if (m <= A.mR && blk * TC_T < A.polar_slots) return;  // the Reinsch-form kernel covers these slots
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool rec = warp < 4, issuer = warp == TA_NT / 32 - 1;
+    const bool rec = warp < 4, splitw = warp >= 4 && warp < 12, epi = warp >= 12 && warp < 16;
+    const bool issuer = warp == 16;
     const int sp = tid - TC_T;                              // split-thread index 0..255
     const int r = rec ? tid : (sp & (TC_T - 1));            // slot within the block
     const int slot = blk * TC_T + r;
@@ -856,7 +896,7 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
     const int cfirst = A.first[m * A.nblk + blk];           // chunks before it hold only dropped values
     const int nlive = nch - cfirst;
     const int nm = A.nmaps;
-    float4 *part = A.partial + (int64_t)blk * A.nalm * nm;  // this block's [index][map]
+    float4 *part = A.partial + (int64_t)blk * A.nalm_part * nm - A.idx0 * nm;  // this block's [index][map]
 
     // l before the first live chunk: zero partials
     {
@@ -872,10 +912,13 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < TA_NB; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[i])), "r"(1));          // commit
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(2 * TC_T));   // split threads
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfree[i])), "r"(2 * TC_T));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfree[i])), "r"(TA_NEPI));  // epilogue
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(1));         // commit
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -891,22 +934,23 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
     } else if (issuer) {
         // ------------------------------------------------ MMA issue (one lane of the last warp)
         // per chunk q: wait until accumulator set q & 1 is read out (chunk q - 2), then per K-step
-        // until its y tile is written, issue its 10 MMAs and commit them to the buffer's done
-        // barrier.  The whole warp runs the loop (descriptors are base values plus constant
-        // offsets of the address field, kept warp-uniform); one elected lane issues.
+        // until its y tile is written, issue its 10 MMAs and commit them to the tile's done barrier,
+        // and after the chunk's last K-step to the set's afull barrier.  The whole warp runs the
+        // loop (descriptors are base values plus constant offsets of the address field, kept
+        // warp-uniform); one elected lane issues.
         const uint32_t idesc = umma_idesc<TA_N>();  // M = 128, N = 64
         const uint64_t dA0 = umma_desc(smem_u32(sX), TA_XKB, 128);
         const uint64_t dB0 = umma_desc(smem_u32(sY), TA_BKB, 128);
         const uint32_t issue = elect_one();
-        for (int q = 0; q < nlive; ++q) {
+        for (int q = 0; q < nlive && ok; ++q) {
             const int st = q & 1;
             if (q >= 2 && ok && !mbar_wait(&tfree[st], (uint32_t)(((q - 2) >> 1) & 1))) ok = false;
             ok = __all_sync(0xffffffffu, ok);
             const uint32_t dt = tmem + (uint32_t)(st * TA_ACC);
 #pragma unroll 1
-            for (int kk = 0; kk < TC_T / 16; ++kk) {
-                const int gk = 8 * q + kk, b = gk & 1;
-                if (ok && !mbar_wait(&full[b], (uint32_t)((gk >> 1) & 1))) ok = false;
+            for (int kk = 0; kk < TC_T / 16 && ok; ++kk) {
+                const int gk = 8 * q + kk, b = gk % TA_NB;
+                if (!mbar_wait(&full[b], (uint32_t)((gk / TA_NB) & 1))) ok = false;
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -922,11 +966,12 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                     }
                 }
                 umma_commit_by(issue, &mbar[b]);
+                if (kk == TC_T / 16 - 1) umma_commit_by(issue, &afull[st]);
             }
         }
         if (lane == 0 && !ok) atomicOr(A.status, 1);
-    } else {
-        // ------------------------------------------------ X digits, then split / epilogue
+    } else if (splitw) {
+        // ------------------------------------------------ X digits, then the y tiles
         const int Ey = A.Ey[m * A.nblk + blk];
         const int hh = sp >> 7;  // this thread's maps: 8 hh .. 8 hh + 7 of slot r (uniform per warp)
         double xv[2][8][2];      // [Sigma, D][map][re, im] -> row 32 s + 2 g + c
@@ -963,11 +1008,11 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
             const int kb = t / (TA_R / 8 * 8), rest = t - kb * (TA_R / 8 * 8);
             *(uint4 *)(sX + kb * TA_XKB + (TC_S * (TA_R / 8)) * 128 + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (sp < 2 * 2 * TA_BDIG / 16) {  // [buffer][8-slot group]
+        if (sp < TA_NB * 2 * TA_BDIG / 16) {  // [buffer][8-slot group]
             const int g2 = sp / (TA_BDIG / 16), rest = sp - g2 * (TA_BDIG / 16);
             *(uint4 *)(sY + g2 * TA_BKB + TC_S * TA_BDIG + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
         }
-        bar_sync(BAR_SPLIT, 2 * TC_T);
+        bar_sync(BAR_PREP, 2 * TC_T + TA_NEPI);  // row exponents complete (the epilogue reads them too)
         // A operand, K-major: element (row, k = r) of digit q in core matrix (q * 8 + row / 8) of
         // 8-slot group r / 8, so that digits q and q + 1 form one 128-row operand
 #pragma unroll
@@ -993,60 +1038,16 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
         const int n = 8 * nhi + nlo;
         const int jrow = 2 * (n & 15) + (n >> 4);
         const int boff = kh * TA_BKB + nhi * 128 + nlo * 16 + kp * 4;
-        // epilogue: lane quarter qd (warps w and w + 4 share one); row 32 (qd & 1) + lane, the top
-        // half (qd < 2) or the bottom half (qd >= 2) of its sums; Sigma rows (qd even) keep the even
-        // l - m columns 0-15, D rows the odd ones 16-31; this warp takes 8 of them from n0
-        const int qd = warp & 3, hf = w8 >> 2;
-        const int es = qd & 1;
-        const int erow = 32 * es + lane;
-        const int eg = lane >> 1, ec = lane & 1;
-        const int n0 = 16 * es + 8 * hf;
-        for (int q = 0; q <= nlive; ++q) {
+        for (int q = 0; q < nlive; ++q) {
             const int st = q & 1;
-            if (q < nlive) bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
-            if (q >= 1) {
-                // ---- epilogue of chunk q - 1: the commit of its last K-step covers all its MMAs
-                const int qe = q - 1, tb = qe & 1, gl = 8 * qe + 7;
-                if (ok && !mbar_wait(&mbar[gl & 1], (uint32_t)((gl >> 1) & 1))) ok = false;
-                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-wide
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                float2 acc[8];
-                if (ok) read_regions(tmem, qd, tb, n0, acc);
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[tb])) : "memory");
-                if (ok && qd >= 2) {
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) xch[(8 * hf + t) * TA_R + erow] = acc[t];
-                }
-                bar_sync(BAR_SPLIT, 2 * TC_T);  // bottom sums in xch
-                if (ok && qd < 2) {
-                    // value = (top + bottom) 2^(Ey + Ex - 12): a power of two, applied to hi and lo
-                    const int ex = sEx[erow];
-                    const int e = Ey + (ex ? ex - 1022 : -1000) - 12;
-                    const float sc = (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.f;
-                    if (eg < nm) {
-                        const int l0 = m + TC_CH * (cfirst + qe);
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            const float2 v = df_sum(acc[t], xch[(8 * hf + t) * TA_R + erow]);
-                            const int l = l0 + 2 * ((n0 + t) & 15) + es;
-                            if (l <= L) {
-                                float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
-                                *dst = make_float2(v.x * sc, v.y * sc);
-                            }
-                        }
-                    }
-                }
-            }
-            if (q == nlive) break;
-            // ---- the 8 y tiles of chunk q
+            bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
             const double *yb = ybuf + (size_t)st * TC_CH * TA_YS;
 #pragma unroll 1
             for (int kk = 0; kk < TC_T / 16; ++kk) {
-                const int gk = 8 * q + kk, b = gk & 1;
+                const int gk = 8 * q + kk, b = gk % TA_NB;
                 unsigned char *yt = sY + b * TA_BTILE;
-                // the MMAs of K-step gk - 2 read this buffer: wait (bounded) before rewriting it
-                if (gk >= 2 && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk >> 1) - 1) & 1))) ok = false;
+                // the MMAs of K-step gk - NB read this buffer: wait (bounded) before rewriting it
+                if (gk >= TA_NB && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk / TA_NB) - 1) & 1))) ok = false;
                 const double2 yy = *reinterpret_cast<const double2 *>(yb + jrow * TA_YS + 16 * kk + 8 * kh + 2 * kp);
                 float d0[TC_S], d1[TC_S];
                 split_digits(yy.x, Ey, d0);
@@ -1060,7 +1061,48 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                 asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
             }
         }
-        if (!ok && (tid & 31) == 0) atomicOr(A.status, 1);
+        if (!ok && lane == 0) atomicOr(A.status, 1);
+    } else if (epi) {
+        // ------------------------------------------------ epilogue, one warp per lane quarter
+        // lane quarter qd: row 32 (qd & 1) + lane, the top half (qd < 2) or the bottom half (qd >= 2)
+        // of its sums; Sigma rows (qd even) keep the even l - m columns 0-15, D rows the odd 16-31
+        const int qd = warp & 3, es = qd & 1;
+        const int erow = 32 * es + lane;
+        const int eg = lane >> 1, ec = lane & 1;
+        bar_sync(BAR_PREP, 2 * TC_T + TA_NEPI);  // row exponents complete
+        // value = (top + bottom) 2^(Ey + Ex - 12): a power of two, applied to hi and lo
+        const int ex = sEx[erow];
+        const int e = A.Ey[m * A.nblk + blk] + (ex ? ex - 1022 : -1000) - 12;
+        const float sc = (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.f;
+        for (int q = 0; q < nlive; ++q) {
+            const int tb = q & 1;
+            if (ok && !mbar_wait(&afull[tb], (uint32_t)((q >> 1) & 1))) ok = false;
+            ok = bar_red_and(BAR_EPI, TA_NEPI, ok);  // the four warps agree (tcgen05.ld is warp-wide)
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            float2 acc[16];
+            if (ok) read_regions(tmem, qd, tb, es, acc);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[tb])) : "memory");
+            bar_sync(BAR_EPI, TA_NEPI);  // the top warps have read the previous chunk's exchange
+            if (ok && qd >= 2) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) xch[t * TA_R + erow] = acc[t];
+            }
+            bar_sync(BAR_EPI, TA_NEPI);  // bottom sums in xch
+            if (ok && qd < 2 && eg < nm) {
+                const int l0 = m + TC_CH * (cfirst + q);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float2 v = df_sum(acc[t], xch[t * TA_R + erow]);
+                    const int l = l0 + 2 * t + es;
+                    if (l <= L) {
+                        float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
+                        *dst = make_float2(v.x * sc, v.y * sc);
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicOr(A.status, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -1104,19 +1146,55 @@ static int64_t polar_alm_count(const Plan &p)
     return mR < 0 ? 0 : (int64_t)(mR + 1) * (2 * (int64_t)p.lmax + 3 - (mR + 1)) / 2;
 }
 
-// partial a_lm / c_lm per 128-slot block for one group of up to 16 maps (reduced per group),
+// The tensor-core analysis runs in m-slabs of about equal coefficient counts, each followed by its
+// block reduction, so that the partial sums of one slab only are held at a time: at lmax 4096 all
+// 32 blocks x 16 maps x 16 B per coefficient would take 69 GB, a slab about 1/8 of that.  The
+// first slab covers every m of the Reinsch-form polar slots.  Boundaries: first m of each slab,
+// then mmax + 1.
+static std::vector<int> anal_slabs(const Plan &p)
+{
+    const int nblk = (p.nslots + TC_T - 1) / TC_T;
+    const int64_t full = (int64_t)nblk * TA_MAPS * p.nalm * (int64_t)sizeof(float4);
+    const int ns = full <= (int64_t(2) << 30) ? 1 : 8;
+    const int64_t L = p.lmax;
+    auto idx = [&](int64_t m) { return m * (2 * L + 3 - m) / 2; };
+    const int mR = p.polar_first_slot ? p.mR : -1;
+    std::vector<int> b{0};
+    for (int k = 1; k < ns; ++k) {
+        const int64_t want = p.nalm * k / ns;
+        int m = b.back() + 1;
+        while (m <= p.mmax && idx(m) < want) ++m;
+        m = std::max(m, mR + 1);
+        if (m > b.back() && m <= p.mmax) b.push_back(m);
+    }
+    b.push_back(p.mmax + 1);
+    return b;
+}
+
+static int64_t slab_max_count(const Plan &p)
+{
+    const std::vector<int> b = anal_slabs(p);
+    const int64_t L = p.lmax;
+    auto idx = [&](int64_t m) { return m * (2 * L + 3 - m) / 2; };
+    int64_t mx = 0;
+    for (size_t k = 0; k + 1 < b.size(); ++k) mx = std::max(mx, (b[k + 1] > p.mmax ? p.nalm : idx(b[k + 1])) - idx(b[k]));
+    return mx;
+}
+
+// partial a_lm / c_lm per 128-slot block for one group of up to 16 maps and one m-slab,
 // [block][index][map] float4, then the Reinsch-form partials of the first polar slots for
 // m <= mR, [map][index] double2
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps)
 {
     const int nblk = (p.nslots + TC_T - 1) / TC_T;
     const size_t nm = (size_t)std::min(nmaps, TA_MAPS);
-    return (size_t)nblk * nm * (size_t)p.nalm * sizeof(float4) + nm * (size_t)polar_alm_count(p) * sizeof(double2);
+    return (size_t)nblk * nm * (size_t)slab_max_count(p) * sizeof(float4) +
+           nm * (size_t)polar_alm_count(p) * sizeof(double2);
 }
 
-// The precision-form analysis on the tensor cores: per group of up to 16 maps, the tensor-core
-// kernel for every slot block outside the polar slots (m <= mR), the double-float Reinsch-form
-// kernel for those, then the fixed-order block reduction into a_lm.
+// The precision-form analysis on the tensor cores: per group of up to 16 maps, the double-float
+// Reinsch-form kernel for the polar slots (m <= mR), then per m-slab the tensor-core kernel for every
+// other slot block and the fixed-order block reduction of that slab into a_lm.
 cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch)
 {
@@ -1143,34 +1221,45 @@ cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2
     A.nalm = p.nalm;
     const int64_t dstride = (int64_t)p.nrings * (p.mmax + 1);
     const int64_t fp64_lim = polar_alm_count(p);
+    const std::vector<int> slabs = anal_slabs(p);
+    const int64_t smax = slab_max_count(p);
+    const int64_t L = p.lmax;
+    auto idx = [&](int64_t m) { return m * (2 * L + 3 - m) / 2; };
     for (int g0 = 0; g0 < nmaps; g0 += TA_MAPS) {
         const int nm = std::min(TA_MAPS, nmaps - g0);
         A.nmaps = nm;
         A.delta = const_cast<double2 *>(delta) + (int64_t)g0 * dstride;
         A.partial = (float4 *)partial;
-        {
-            StageEvents ev(p, SHT_STAGE_TC_ANAL_KERNEL, st);
-            tc_anal_kernel<<<(unsigned)((p.mmax + 1) * A.nblk), TA_NT, TA_SMEM, st>>>(A);
-            p.launches[SHT_STAGE_TC_ANAL_KERNEL] += 1;
-            ev.done();
-        }
-        ++*nlaunch;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        cudaError_t e;
         double2 *polar = nullptr;
         if (fp64_lim > 0) {
             int n = 0;
-            polar = (double2 *)(A.partial + (int64_t)A.nblk * nm * p.nalm);
+            polar = (double2 *)(A.partial + (int64_t)A.nblk * nm * smax);
             e = launch_legendre_anal_df_polar(p, A.delta, polar, fp64_lim, nm, st, &n);
             *nlaunch += n;
             if (e != cudaSuccess) return e;
         }
-        // partial (block, map g, index i) at block * nalm nm + i nm + g
-        e = launch_reduce_blocks_df(A.partial, polar, fp64_lim, A.polar_slots / TC_T, p.d_cfac,
-                                    alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm, nm, p.lmax, (int64_t)nm * p.nalm, 1,
-                                    nm, fp64_lim, st);
-        ++*nlaunch;
-        if (e != cudaSuccess) return e;
+        for (size_t k = 0; k + 1 < slabs.size(); ++k) {
+            const int mlo = slabs[k], mhi = slabs[k + 1];
+            A.m0 = mlo;
+            A.idx0 = idx(mlo);
+            A.nalm_part = (mhi > p.mmax ? p.nalm : idx(mhi)) - A.idx0;
+            {
+                StageEvents ev(p, SHT_STAGE_TC_ANAL_KERNEL, st);
+                tc_anal_kernel<<<(unsigned)((mhi - mlo) * A.nblk), TA_NT, TA_SMEM, st>>>(A);
+                p.launches[SHT_STAGE_TC_ANAL_KERNEL] += 1;
+                ev.done();
+            }
+            ++*nlaunch;
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            // partial (block, map g, index i) at block * nalm_part nm + (i - idx0) nm + g
+            e = launch_reduce_blocks_df(A.partial, polar, fp64_lim, A.polar_slots / TC_T, p.d_cfac,
+                                        alm + (int64_t)g0 * p.nalm, A.nblk, p.nalm, nm, p.lmax,
+                                        (int64_t)nm * A.nalm_part, 1, nm, fp64_lim, st, A.idx0, A.nalm_part);
+            ++*nlaunch;
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -1189,14 +1278,14 @@ cudaError_t build_tc_scales(Plan &p)
     A.mmax = p.mmax;
     int *ey = nullptr;  // [2][mmax + 1][nblk]: y exponents, then first live chunks
     const size_t n = (size_t)(p.mmax + 1) * A.nblk;
-    cudaError_t e = cudaMalloc(&ey, sizeof(int) * 2 * n);
+    cudaError_t e = sht::dev_malloc(&ey, sizeof(int) * 2 * n);
     if (e != cudaSuccess) return e;
     tc_ymax_kernel<<<(unsigned)n, TC_T>>>(A, ey, ey + n);
     e = cudaGetLastError();
     double2 *cky = nullptr;
     int *ckk = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&cky, sizeof(double2) * n * TC_T);
-    if (e == cudaSuccess) e = cudaMalloc(&ckk, sizeof(int) * n * TC_T);
+    if (e == cudaSuccess) e = sht::dev_malloc(&cky, sizeof(double2) * n * TC_T);
+    if (e == cudaSuccess) e = sht::dev_malloc(&ckk, sizeof(int) * n * TC_T);
     if (e == cudaSuccess) {
         tc_ckpt_kernel<<<(unsigned)n, TC_T>>>(A, ey + n, cky, ckk);
         e = cudaGetLastError();

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <map>
+#include <vector>
 
 namespace sht {
 namespace {
@@ -301,43 +302,98 @@ __device__ __forceinline__ typename P::C fold_bin(const double2 *__restrict__ d,
     return c;
 }
 
+// one unit of the ring synthesis: map g of FFT item `item` (one or two rings)
+template <class P>
+__device__ void ring_synth_unit(const RingArgs<P> &A, int item, int g, typename P::C *B0, typename P::C *B1,
+                                typename P::C *B2)
+{
+    using C = typename P::C;
+    const int64_t mstride = A.mmax + 1;
+    const FftItem it = A.items[item];
+    const FftLen &F = A.lens[it.len_id];
+    const int n = it.n;
+    const double2 *dA = A.delta_in + ((int64_t)g * A.nrings + it.ringA) * mstride;
+    const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
+    const double2 *dB = it.ringB >= 0 ? A.delta_in + ((int64_t)g * A.nrings + it.ringB) * mstride : nullptr;
+    const typename P::T *pB = it.ringB >= 0 ? A.phase + (int64_t)it.ringB * mstride : nullptr;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const C ca = fold_bin<P>(dA, pA, k, n, A.mmax);
+        C z = ca;
+        if (dB) {
+            const C cb = fold_bin<P>(dB, pB, k, n, A.mmax);
+            z = P::add(ca, P::itimes(cb));  // C_A + i C_B
+        }
+        B0[k] = z;
+    }
+    __syncthreads();
+    const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);
+    double *outA = A.map_out + (int64_t)g * A.npix + A.ofs[it.ringA];
+    double *outB = it.ringB >= 0 ? A.map_out + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const C z = X[j];
+        outA[j] = P::re(z);
+        if (outB) outB[j] = P::im(z);
+    }
+    __syncthreads();
+}
+
 template <class P>
 __global__ void __launch_bounds__(FFT_T) ring_synth_kernel(RingArgs<P> A)
 {
     using C = typename P::C;
     C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
     C *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
-    const int64_t mstride = A.mmax + 1;
     const int nunits = A.nitems * A.nmaps;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int item = unit / A.nmaps, g = unit - item * A.nmaps;
-        const FftItem it = A.items[item];
-        const FftLen &F = A.lens[it.len_id];
-        const int n = it.n;
-        const double2 *dA = A.delta_in + ((int64_t)g * A.nrings + it.ringA) * mstride;
-        const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
-        const double2 *dB = it.ringB >= 0 ? A.delta_in + ((int64_t)g * A.nrings + it.ringB) * mstride : nullptr;
-        const typename P::T *pB = it.ringB >= 0 ? A.phase + (int64_t)it.ringB * mstride : nullptr;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const C ca = fold_bin<P>(dA, pA, k, n, A.mmax);
-            C z = ca;
-            if (dB) {
-                const C cb = fold_bin<P>(dB, pB, k, n, A.mmax);
-                z = P::add(ca, P::itimes(cb));  // C_A + i C_B
-            }
-            B0[k] = z;
-        }
-        __syncthreads();
-        const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);
-        double *outA = A.map_out + (int64_t)g * A.npix + A.ofs[it.ringA];
-        double *outB = it.ringB >= 0 ? A.map_out + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const C z = X[j];
-            outA[j] = P::re(z);
-            if (outB) outB[j] = P::im(z);
-        }
-        __syncthreads();
+        ring_synth_unit<P>(A, item, g, B0, B1, B2);
     }
+}
+
+// one unit of the ring analysis: map g of FFT item `item`
+template <class P>
+__device__ void ring_anal_unit(const RingArgs<P> &A, int item, int g, typename P::C *B0, typename P::C *B1,
+                               typename P::C *B2)
+{
+    using C = typename P::C;
+    const int64_t mstride = A.mmax + 1;
+    const FftItem it = A.items[item];
+    const FftLen &F = A.lens[it.len_id];
+    const int n = it.n;
+    const double *sA = A.map_in + (int64_t)g * A.npix + A.ofs[it.ringA];
+    const double *sB = it.ringB >= 0 ? A.map_in + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        B0[j] = P::from_re_im(sA[j], sB ? -sB[j] : 0.0);  // conj(s_A + i s_B)
+    __syncthreads();
+    const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);  // conj(S)
+    const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
+    double2 *oA = A.delta_out + ((int64_t)g * A.nrings + it.ringA) * mstride;
+    const double wA = A.w[it.ringA];
+    if (it.ringB < 0) {
+        for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
+            const C S = P::conj(X[m % n]);
+            const double2 v = P::to(P::mulc(P::conjt(pA[m]), S));
+            oA[m] = make_double2(wA * v.x, m == 0 ? 0.0 : wA * v.y);
+        }
+    } else {
+        const typename P::T *pB = A.phase + (int64_t)it.ringB * mstride;
+        double2 *oB = A.delta_out + ((int64_t)g * A.nrings + it.ringB) * mstride;
+        const double wB = A.w[it.ringB];
+        for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
+            const int k = m % n;
+            const int kc = (n - k) % n;
+            const C S = P::conj(X[k]);
+            const C Sc = X[kc];  // conj(S_{-k})
+            const C SA = P::half(P::add(S, Sc));
+            const C D = P::half(P::sub(S, Sc));
+            const C SB = P::conj(P::itimes(P::conj(D)));  // D / (2 i) with D halved: -i D
+            const double2 va = P::to(P::mulc(P::conjt(pA[m]), SA));
+            const double2 vb = P::to(P::mulc(P::conjt(pB[m]), SB));
+            oA[m] = make_double2(wA * va.x, m == 0 ? 0.0 : wA * va.y);
+            oB[m] = make_double2(wB * vb.x, m == 0 ? 0.0 : wB * vb.y);
+        }
+    }
+    __syncthreads();
 }
 
 template <class P>
@@ -346,47 +402,35 @@ __global__ void __launch_bounds__(FFT_T) ring_anal_kernel(RingArgs<P> A)
     using C = typename P::C;
     C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
     C *B1 = B0 + A.maxlen, *B2 = B1 + A.maxlen;
-    const int64_t mstride = A.mmax + 1;
     const int nunits = A.nitems * A.nmaps;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int item = unit / A.nmaps, g = unit - item * A.nmaps;
-        const FftItem it = A.items[item];
-        const FftLen &F = A.lens[it.len_id];
-        const int n = it.n;
-        const double *sA = A.map_in + (int64_t)g * A.npix + A.ofs[it.ringA];
-        const double *sB = it.ringB >= 0 ? A.map_in + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
-        for (int j = threadIdx.x; j < n; j += blockDim.x)
-            B0[j] = P::from_re_im(sA[j], sB ? -sB[j] : 0.0);  // conj(s_A + i s_B)
+        ring_anal_unit<P>(A, item, g, B0, B1, B2);
+    }
+}
+
+// batched form: units (job, item, map) of many plans from one device counter, in the host's order
+// (longest rings first); every CTA keeps its own three scratch buffers of `maxlen` entries
+template <class P, bool SYNTH>
+__global__ void __launch_bounds__(FFT_T) ring_batch_kernel(const RingArgs<P> *__restrict__ jobs,
+                                                           const int4 *__restrict__ units, int nunits, int maxlen,
+                                                           typename P::C *scratch, int *counter)
+{
+    using C = typename P::C;
+    __shared__ int s_t;
+    C *B0 = scratch + (int64_t)blockIdx.x * 3 * maxlen;
+    C *B1 = B0 + maxlen, *B2 = B1 + maxlen;
+    for (;;) {
         __syncthreads();
-        const C *X = cta_dft<P>(F, A.tab, B0, B1, B2);  // conj(S)
-        const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
-        double2 *oA = A.delta_out + ((int64_t)g * A.nrings + it.ringA) * mstride;
-        const double wA = A.w[it.ringA];
-        if (it.ringB < 0) {
-            for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
-                const C S = P::conj(X[m % n]);
-                const double2 v = P::to(P::mulc(P::conjt(pA[m]), S));
-                oA[m] = make_double2(wA * v.x, m == 0 ? 0.0 : wA * v.y);
-            }
-        } else {
-            const typename P::T *pB = A.phase + (int64_t)it.ringB * mstride;
-            double2 *oB = A.delta_out + ((int64_t)g * A.nrings + it.ringB) * mstride;
-            const double wB = A.w[it.ringB];
-            for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
-                const int k = m % n;
-                const int kc = (n - k) % n;
-                const C S = P::conj(X[k]);
-                const C Sc = X[kc];  // conj(S_{-k})
-                const C SA = P::half(P::add(S, Sc));
-                const C D = P::half(P::sub(S, Sc));
-                const C SB = P::conj(P::itimes(P::conj(D)));  // D / (2 i) with D halved: -i D
-                const double2 va = P::to(P::mulc(P::conjt(pA[m]), SA));
-                const double2 vb = P::to(P::mulc(P::conjt(pB[m]), SB));
-                oA[m] = make_double2(wA * va.x, m == 0 ? 0.0 : wA * va.y);
-                oB[m] = make_double2(wB * vb.x, m == 0 ? 0.0 : wB * vb.y);
-            }
-        }
+        if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
         __syncthreads();
+        const int t = s_t;
+        if (t >= nunits) break;
+        const int4 U = units[t];
+        if (SYNTH)
+            ring_synth_unit<P>(jobs[U.x], U.y, U.z, B0, B1, B2);
+        else
+            ring_anal_unit<P>(jobs[U.x], U.y, U.z, B0, B1, B2);
     }
 }
 
@@ -587,8 +631,8 @@ cudaError_t build_df_ring_tables(Plan &p)
     const int64_t nph = (int64_t)p.nrings * (p.mmax + 1);
     const int64_t ntab = std::max<int64_t>(p.fft_tab_len, 1);
     float4 *tab = nullptr, *ph = nullptr;
-    cudaError_t e = cudaMalloc(&tab, sizeof(float4) * ntab);
-    if (e == cudaSuccess) e = cudaMalloc(&ph, sizeof(float4) * nph);
+    cudaError_t e = sht::dev_malloc(&tab, sizeof(float4) * ntab);
+    if (e == cudaSuccess) e = sht::dev_malloc(&ph, sizeof(float4) * nph);
     if (e == cudaSuccess) {
         df_table_kernel<<<152 * 8, 256>>>(p.d_fft_tab, tab, p.fft_tab_len);
         df_table_kernel<<<152 * 8, 256>>>(p.d_phase, ph, nph);
@@ -610,8 +654,8 @@ cudaError_t build_phase_table(Plan &p)
     cudaError_t e;
     double *d_phi0 = nullptr;
     const size_t bytes = (size_t)p.nrings * (p.mmax + 1) * sizeof(double2);
-    if ((e = cudaMalloc(&p.d_phase, bytes)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&d_phi0, p.nrings * sizeof(double))) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&p.d_phase, bytes)) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&d_phi0, p.nrings * sizeof(double))) != cudaSuccess) return e;
     e = cudaMemcpy(d_phi0, p.phi0.data(), p.nrings * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         phase_table_kernel<<<152 * 8, 256>>>(d_phi0, p.nrings, p.mmax, p.d_phase);
@@ -691,15 +735,15 @@ cudaError_t build_fft_tables(Plan &p)
     TabJob *d_jobs = nullptr;
     int *d_blue = nullptr;
     double2 *d_scr = nullptr;
-    if ((e = cudaMalloc(&p.d_items, sizeof(FftItem) * items.size())) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p.d_lens, sizeof(FftLen) * p.lens.size())) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p.d_fft_tab, sizeof(double2) * std::max<int64_t>(off, 1))) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&p.d_items, sizeof(FftItem) * items.size())) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&p.d_lens, sizeof(FftLen) * p.lens.size())) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&p.d_fft_tab, sizeof(double2) * std::max<int64_t>(off, 1))) != cudaSuccess) return e;
     if ((e = cudaMemcpy(p.d_items, items.data(), sizeof(FftItem) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     if ((e = cudaMemcpy(p.d_lens, p.lens.data(), sizeof(FftLen) * p.lens.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaMalloc(&d_jobs, sizeof(TabJob) * jobs.size())) != cudaSuccess) return e;
+    if ((e = sht::dev_malloc(&d_jobs, sizeof(TabJob) * jobs.size())) != cudaSuccess) return e;
     e = cudaMemcpy(d_jobs, jobs.data(), sizeof(TabJob) * jobs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         fill_tables_kernel<<<(unsigned)std::min<size_t>(jobs.size(), 152 * 8), 256>>>(d_jobs, (int)jobs.size(),
@@ -708,9 +752,9 @@ cudaError_t build_fft_tables(Plan &p)
     }
     if (e == cudaSuccess && !blue_ids.empty()) {
         const int g = (int)std::min<size_t>(blue_ids.size(), 152);
-        e = cudaMalloc(&d_blue, sizeof(int) * blue_ids.size());
+        e = sht::dev_malloc(&d_blue, sizeof(int) * blue_ids.size());
         if (e == cudaSuccess) e = cudaMemcpy(d_blue, blue_ids.data(), sizeof(int) * blue_ids.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&d_scr, (size_t)g * 3 * maxlen * sizeof(double2));
+        if (e == cudaSuccess) e = sht::dev_malloc(&d_scr, (size_t)g * 3 * maxlen * sizeof(double2));
         if (e == cudaSuccess) {
             bluestein_filter_kernel<<<g, FFT_T>>>(p.d_lens, d_blue, (int)blue_ids.size(), p.d_fft_tab, d_scr, maxlen);
             e = cudaGetLastError();
@@ -721,6 +765,65 @@ cudaError_t build_fft_tables(Plan &p)
     cudaFree(d_blue);
     cudaFree(d_scr);
     return e;
+}
+
+// ---------------------------------------------------------------- batched form: host side
+
+cudaError_t batch_ring_setup(const std::vector<const Plan *> &plans, const std::vector<const void *> &in,
+                             const std::vector<void *> &out, const std::vector<int> &nmaps, bool synth,
+                             BatchLaunch &L, int &maxlen)
+{
+    std::vector<RingArgs<F64>> jobs(plans.size());
+    struct Key {
+        int n;
+        int4 u;
+    };
+    std::vector<Key> keys;
+    maxlen = 1;
+    for (size_t j = 0; j < plans.size(); ++j) {
+        const Plan &p = *plans[j];
+        RingArgs<F64> A = ring_args<F64>(p, p.d_fft_tab, p.d_phase, nullptr, nmaps[j]);
+        if (synth) {
+            A.delta_in = (const double2 *)in[j];
+            A.map_out = (double *)out[j];
+        } else {
+            A.map_in = (const double *)in[j];
+            A.delta_out = (double2 *)out[j];
+        }
+        jobs[j] = A;
+        maxlen = std::max(maxlen, p.fft_maxlen);
+        std::vector<FftItem> items(p.nitems);
+        cudaError_t e = cudaMemcpy(items.data(), p.d_items, sizeof(FftItem) * p.nitems, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        for (int i = 0; i < p.nitems; ++i) {
+            const FftLen &F = p.lens[items[i].len_id];
+            const int cost = F.M ? 3 * F.M : F.n;  // Bluestein runs three DFTs of length M
+            for (int g = 0; g < nmaps[j]; ++g) keys.push_back({cost, make_int4((int)j, i, g, 0)});
+        }
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) { return a.n > b.n; });
+    std::vector<int4> units(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) units[i] = keys[i].u;
+    L.ntiles = (int)units.size();
+    cudaError_t e = dev_malloc((RingArgs<F64> **)&L.jobs, sizeof(RingArgs<F64>) * std::max<size_t>(jobs.size(), 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L.jobs, jobs.data(), sizeof(RingArgs<F64>) * jobs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dev_malloc(&L.tiles, sizeof(int4) * std::max<size_t>(units.size(), 1));
+    if (e == cudaSuccess && !units.empty())
+        e = cudaMemcpy(L.tiles, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+cudaError_t batch_ring_launch(const BatchLaunch &L, bool synth, double2 *scratch, int maxlen, int *counter, int grid,
+                              cudaStream_t st)
+{
+    if (synth)
+        ring_batch_kernel<F64, true><<<grid, FFT_T, 0, st>>>((const RingArgs<F64> *)L.jobs, L.tiles, L.ntiles, maxlen,
+                                                             scratch, counter);
+    else
+        ring_batch_kernel<F64, false><<<grid, FFT_T, 0, st>>>((const RingArgs<F64> *)L.jobs, L.tiles, L.ntiles,
+                                                              maxlen, scratch, counter);
+    return cudaGetLastError();
 }
 
 }  // namespace sht

@@ -11,6 +11,16 @@
 
 namespace sht {
 
+// Every device allocation of the library goes through here: cudaMalloc, unless the host-side fault
+// injector (sht_debug_fail_allocations_after) says this one fails, in which case it returns
+// cudaErrorMemoryAllocation without allocating.
+cudaError_t dev_malloc(void **ptr, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T **ptr, size_t bytes)
+{
+    return dev_malloc((void **)ptr, bytes);
+}
+
 // One complex FFT of length n on the ring stage: ring ringA rides on the real
 // part and ringB (or -1) on the imaginary part (two real rings per complex
 // transform).
@@ -152,13 +162,14 @@ size_t tc_workspace_bytes(const Plan &p, int nmaps);
 cudaError_t launch_legendre_anal_tc(const Plan &p, const double2 *delta, double2 *alm, void *partial, int nmaps,
                                     cudaStream_t st, int *nlaunch);
 size_t tc_anal_partial_bytes(const Plan &p, int nmaps);
-// a_lm = c_lm * sum over blocks of double-float partials; partial (block, map, index) at
-// block * blk_stride + map * map_stride + index * idx_stride; for index < fp64_lim blocks
-// 0 .. polar_blocks - 1 are replaced by the FP64 partial polar[map * polar_stride + index]
+// a_lm = c_lm * sum over blocks of double-float partials for the coefficient indices
+// i0 .. i0 + nidx - 1 (nidx < 0: to nalm); partial (block, map, index i) at
+// block * blk_stride + map * map_stride + (i - i0) * idx_stride; for i < fp64_lim blocks
+// 0 .. polar_blocks - 1 are replaced by the FP64 partial polar[map * polar_stride + i]
 cudaError_t launch_reduce_blocks_df(const float4 *partial, const double2 *polar, int64_t polar_stride,
                                     int polar_blocks, const double *cfac, double2 *alm, int nblk, int64_t nalm,
                                     int nmaps, int lmax, int64_t blk_stride, int64_t map_stride, int64_t idx_stride,
-                                    int64_t fp64_lim, cudaStream_t st);
+                                    int64_t fp64_lim, cudaStream_t st, int64_t i0 = 0, int64_t nidx = -1);
 // precision-form Reinsch analysis of the first legendre_anal_df_polar_slots() slots for m <= mR
 int legendre_anal_df_polar_slots();
 cudaError_t launch_legendre_anal_df_polar(const Plan &p, const double2 *delta, double2 *polar, int64_t polar_stride,
@@ -177,6 +188,41 @@ cudaError_t launch_spin_synth(const Plan &p, const double2 *alm, double2 *delta,
                               int *nlaunch);
 cudaError_t launch_spin_anal(const Plan &p, const double2 *delta, double2 *alm, double2 *partial, int nmaps,
                              cudaStream_t st, int *nlaunch);
+
+// batched form (batch.cu, legendre.cu, ringfft.cu): one persistent launch per stage over the tiles
+// of many plans, taken from a device counter in the host's order (longest first)
+struct BatchLaunch {
+    void *jobs = nullptr;     // device array of per-job kernel arguments
+    int4 *tiles = nullptr;    // device tile list
+    int ntiles = 0;
+    int k = 1;                // analysis: ring slots per thread
+};
+struct BatchReduceJob {
+    const double2 *partial;
+    const double *cfac;
+    double2 *alm;
+    int nblk;
+    int64_t nalm;
+    int nmaps;
+    int lmax;
+    int64_t blk_stride;
+};
+cudaError_t batch_legendre_synth_setup(const std::vector<const Plan *> &plans, const std::vector<const double2 *> &alm,
+                                       const std::vector<double2 *> &delta, const std::vector<int> &nmaps,
+                                       int maps_per_tile, BatchLaunch &L);
+cudaError_t batch_legendre_anal_setup(const std::vector<const Plan *> &plans, const std::vector<const double2 *> &delta,
+                                      const std::vector<double2 *> &partial, const std::vector<double2 *> &alm,
+                                      const std::vector<int> &nmaps, int maps_per_tile, int slots_per_thread,
+                                      BatchLaunch &L, BatchLaunch &R);
+size_t batch_anal_partial_bytes(const Plan &p, int nmaps, int slots_per_thread);
+cudaError_t batch_legendre_synth_launch(const BatchLaunch &L, int *counter, int grid, cudaStream_t st);
+cudaError_t batch_legendre_anal_launch(const BatchLaunch &L, const BatchLaunch &R, int *counter, int grid,
+                                       cudaStream_t st);
+cudaError_t batch_ring_setup(const std::vector<const Plan *> &plans, const std::vector<const void *> &in,
+                             const std::vector<void *> &out, const std::vector<int> &nmaps, bool synth,
+                             BatchLaunch &L, int &maxlen);
+cudaError_t batch_ring_launch(const BatchLaunch &L, bool synth, double2 *scratch, int maxlen, int *counter, int grid,
+                              cudaStream_t st);
 
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st);

@@ -4,12 +4,29 @@
 #include "sht_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
 
 namespace sht {
+
+// allocations left before the injected failure; negative: no injection
+static std::atomic<long> g_alloc_budget{-1};
+
+cudaError_t dev_malloc(void **ptr, size_t bytes)
+{
+    long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) {
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
+    return cudaMalloc(ptr, bytes);
+}
 
 static cudaEvent_t pool_event(const Plan &p)
 {
@@ -102,7 +119,7 @@ void free_plan_device(Plan &p)
 template <class T>
 cudaError_t upload(T **dst, const T *src, size_t n)
 {
-    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(n, 1));
+    cudaError_t e = sht::dev_malloc((void **)dst, sizeof(T) * std::max<size_t>(n, 1));
     if (e != cudaSuccess) return e;
     if (n) e = cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
     return e;
@@ -237,7 +254,7 @@ sht_status ensure_workspace(Plan &p, size_t need)
         p.ws_bytes = 0;
         if (e != cudaSuccess) return cuda_fail(p, e, "workspace free");
     }
-    cudaError_t e = cudaMalloc(&p.d_ws, need);
+    cudaError_t e = sht::dev_malloc(&p.d_ws, need);
     if (e != cudaSuccess) {
         p.d_ws = nullptr;
         cudaGetLastError();
@@ -471,6 +488,11 @@ sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
     return (*status & 1) ? SHT_ETIMEOUT : SHT_OK;
 }
 
+long sht_debug_fail_allocations_after(long n)
+{
+    return sht::g_alloc_budget.exchange(n < 0 ? -1 : n);
+}
+
 sht_status sht_plan_set_mlist(sht_plan_t plan, const int *ms, int n)
 {
     if (!plan || n < 0 || (n > 0 && !ms)) return SHT_EINVAL;
@@ -490,7 +512,7 @@ sht_status sht_plan_set_mlist(sht_plan_t plan, const int *ms, int n)
         flag[ms[i]] = 1;
     }
     if (!p.d_mflag) {
-        cudaError_t e = cudaMalloc(&p.d_mflag, sizeof(int) * flag.size());
+        cudaError_t e = sht::dev_malloc(&p.d_mflag, sizeof(int) * flag.size());
         if (e != cudaSuccess) {
             p.d_mflag = nullptr;
             return cuda_fail(p, e, "m list");

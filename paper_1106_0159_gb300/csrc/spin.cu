@@ -424,8 +424,8 @@ cudaError_t build_spin_tables(Plan &p)
     }
     double4 *dt = nullptr;
     double *ds = nullptr;
-    cudaError_t e = cudaMalloc(&dt, sizeof(double4) * tab.size());
-    if (e == cudaSuccess) e = cudaMalloc(&ds, sizeof(double) * start.size());
+    cudaError_t e = sht::dev_malloc(&dt, sizeof(double4) * tab.size());
+    if (e == cudaSuccess) e = sht::dev_malloc(&ds, sizeof(double) * start.size());
     if (e == cudaSuccess) e = cudaMemcpy(dt, tab.data(), sizeof(double4) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ds, start.data(), sizeof(double) * start.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

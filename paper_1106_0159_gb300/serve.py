@@ -81,8 +81,9 @@ class Server:
     """Scheduler.  Drive it with submit() and poll() (or run_trace() for a timed arrival trace)."""
 
     def __init__(self, backend, max_batch_maps: int = 32, nstreams: int = 2, memory_budget: Optional[int] = None,
-                 batching: bool = True, clock: Callable[[], float] = time.perf_counter):
+                 batching: bool = True, clock: Callable[[], float] = time.perf_counter, keep_results: bool = True):
         self.backend = backend
+        self.keep_results = bool(keep_results)   # False: a finished request keeps its times, not its output
         self.max_batch_maps = int(max_batch_maps)
         self.nstreams = int(nstreams)
         self.batching = bool(batching)
@@ -164,7 +165,7 @@ class Server:
                     if r.status == "cancelled":
                         self.dropped.append(r)
                         continue
-                    r.result = o
+                    r.result = o if self.keep_results else None
                     r.status = "done"
                     self.completed.append(r)
                     finished += 1
@@ -247,9 +248,11 @@ def _percentile(sorted_vals, q):
 
 class TorchBackend:
     """Runs batches with the CUDA library: one plan per (grid, band limit), kept on the device and
-    shared by the stream slots, each slot with its own scratch (sht_alm2map_ws / sht_map2alm_ws);
-    inputs are concatenated on the device, one transform call per batch, results split back per
-    request (device tensors)."""
+    shared by the stream slots.  Each stream slot owns one scratch buffer, sized for the largest
+    plan and used by whichever plan its batch needs (sht_alm2map_ws / sht_map2alm_ws): a slot runs
+    one batch at a time, so the scratch grows with the slots, not with the number of plans.  Inputs
+    are concatenated on the device, one transform call per batch, results split back per request
+    (device tensors)."""
 
     def __init__(self, mode: int = 1, device=None, nstreams: int = 2, budget_fraction: float = 0.8):
         import torch
@@ -261,8 +264,8 @@ class TorchBackend:
         self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(nstreams)]
         self.plans: Dict[Tuple[int, int], Any] = {}
-        self.scratch: Dict[Tuple[Tuple[int, int], int], Any] = {}
-        self.resident: Dict[Tuple[Tuple[int, int], int], int] = {}
+        self.scratch: Dict[int, Any] = {}        # stream slot -> scratch buffer
+        self.resident: Dict[Any, int] = {}
         self.budget_fraction = budget_fraction
 
     def memory_budget(self) -> int:
@@ -286,18 +289,20 @@ class TorchBackend:
         Returns the seconds it took (plan creation is not serving)."""
         torch = self.torch
         t0 = time.perf_counter()
+        need = 0
         for key in keys:
             p = self.plan(key)
-            for slot in range(len(self.streams)):
-                self.scratch[(key, slot)] = p.scratch(max_maps)
-                self.resident[(key, slot)] = p.workspace_bytes(max_maps)
+            self.resident[key] = 0
+            need = max(need, p.workspace_bytes(max_maps))
+        for slot in range(len(self.streams)):
+            self._grow(slot, need)
         small = min(keys, key=lambda k: k[1])
         p = self.plan(small)
         for n in (1, 17):
             if n > max_maps:
                 continue
             a = torch.zeros((n, p.nalm), dtype=torch.complex128, device=self.device)
-            p.map2alm_ws(p.alm2map_ws(a, self.scratch[(small, 0)]), self.scratch[(small, 0)])
+            p.map2alm_ws(p.alm2map_ws(a, self.scratch[0]), self.scratch[0])
         torch.cuda.synchronize(self.device)
         return time.perf_counter() - t0
 
@@ -311,6 +316,15 @@ class TorchBackend:
         self.resident.clear()
         self.torch.cuda.empty_cache()
 
+    def _grow(self, slot, nbytes):
+        cur = self.scratch.get(slot)
+        if cur is None or cur.numel() < nbytes:
+            self.scratch[slot] = None
+            self.torch.cuda.synchronize(self.device)   # the old buffer may still be read by the slot's stream
+            self.scratch[slot] = self.torch.empty((int(nbytes),), dtype=self.torch.uint8, device=self.device)
+            self.resident[("scratch", slot)] = int(nbytes)
+        return self.scratch[slot]
+
     def resident_bytes(self) -> int:
         return sum(self.resident.values())
 
@@ -322,10 +336,7 @@ class TorchBackend:
         torch = self.torch
         p = self.plan(key)
         st = self.streams[slot]
-        scr = self.scratch.get((key, slot))
-        if scr is None or scr.numel() < p.workspace_bytes(sum(nmaps)):
-            scr = self.scratch[(key, slot)] = p.scratch(sum(nmaps))   # a request beyond the warm-up size
-            self.resident[(key, slot)] = scr.numel()
+        scr = self._grow(slot, p.workspace_bytes(sum(nmaps)))   # grows only beyond the warm-up size
         st.wait_stream(torch.cuda.current_stream(self.device))  # inputs were made on the caller's stream
         with torch.cuda.stream(st):
             x = datas[0] if len(datas) == 1 else torch.cat(datas, dim=0)

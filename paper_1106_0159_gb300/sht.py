@@ -37,7 +37,9 @@ EXPORTS = (
     "sht_plan_set_mode", "sht_plan_mode", "sht_plan_device_status", "sht_plan_reserve",
     "sht_plan_set_tuning", "sht_plan_tuning", "sht_plan_selftest_timeout", "sht_alm2map_ws", "sht_map2alm_ws",
     "sht_plan_live_steps", "sht_alm2map_spin", "sht_map2alm_spin", "sht_spin_workspace_bytes",
-    "sht_plan_set_mlist",
+    "sht_plan_set_mlist", "sht_debug_fail_allocations_after",
+    "sht_batch_create", "sht_batch_set_tuning", "sht_batch_tuning", "sht_batch_run", "sht_batch_tiles",
+    "sht_batch_last_error", "sht_batch_destroy",
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
@@ -100,6 +102,14 @@ def load():
             "sht_map2alm_spin": (I, [P, I, P, P, I, P]),
             "sht_spin_workspace_bytes": (S, [P, I]),
             "sht_plan_set_mlist": (I, [P, P, I]),
+            "sht_debug_fail_allocations_after": (ctypes.c_long, [ctypes.c_long]),
+            "sht_batch_create": (I, [ctypes.POINTER(P), I, I, P, P, P, P]),
+            "sht_batch_set_tuning": (I, [P, I, I]),
+            "sht_batch_tuning": (I, [P, I]),
+            "sht_batch_run": (I, [P, P]),
+            "sht_batch_tiles": (I64, [P, I]),
+            "sht_batch_last_error": (ctypes.c_char_p, [P]),
+            "sht_batch_destroy": (None, [P]),
             "sht_plan_device_status": (I, [P, P, I]),
             "sht_plan_reserve": (I, [P, I]),
             "sht_plan_set_tuning": (I, [P, I, I]),
@@ -412,3 +422,74 @@ class Plan:
         o = self._out(out, (d.shape[0], self.nalm), torch.complex128, d)
         self._run(load().sht_legendre_anal, d, o, d.shape[0], stream)
         return o
+
+
+# batched form: knobs of sht_batch_set_tuning and the values each takes
+BATCH_SYNTH_MAPS, BATCH_LEG_CTAS, BATCH_RING_CTAS, BATCH_ANAL_MAPS, BATCH_ANAL_SLOTS = range(5)
+BATCH_TUNE_VALUES = {BATCH_SYNTH_MAPS: (1, 2, 4), BATCH_LEG_CTAS: (2, 4, 8, 16), BATCH_RING_CTAS: (1, 2, 3, 4),
+                     BATCH_ANAL_MAPS: (1, 2), BATCH_ANAL_SLOTS: (1, 4)}
+BATCH_ALM2MAP, BATCH_MAP2ALM = 0, 1
+
+
+class Batch:
+    """Many transforms of one direction as one persistent launch per stage (sht_batch_*).
+
+    jobs: list of (plan, src, dst) with the tensors of plan.alm2map / plan.map2alm (device,
+    contiguous, kept by the batch: write new inputs into src in place between runs)."""
+
+    def __init__(self, direction: int, jobs):
+        import torch
+        self.direction = int(direction)
+        self.jobs = list(jobs)
+        chk = []
+        for plan, src, dst in self.jobs:
+            if self.direction == BATCH_ALM2MAP:
+                a = plan._dev(src, torch.complex128, (plan.nalm,), "alm")
+                o = plan._dev(dst, torch.float64, (plan.npix,), "map")
+            else:
+                a = plan._dev(src, torch.float64, (plan.npix,), "map")
+                o = plan._dev(dst, torch.complex128, (plan.nalm,), "alm")
+            if a.shape[0] != o.shape[0]:
+                raise ValueError("src and dst map counts differ")
+            chk.append((plan, a, o))
+        self.jobs = chk
+        n = len(chk)
+        P = ctypes.c_void_p
+        plans = (P * n)(*[P(p._h.value if hasattr(p._h, "value") else p._h) for p, _, _ in chk])
+        ins = (P * n)(*[P(a.data_ptr()) for _, a, _ in chk])
+        outs = (P * n)(*[P(o.data_ptr()) for _, _, o in chk])
+        nm = (ctypes.c_int * n)(*[int(a.shape[0]) for _, a, _ in chk])
+        self._h = P()
+        _check(load().sht_batch_create(ctypes.byref(self._h), self.direction, n, plans, ins, outs, nm), None,
+               "sht_batch_create")
+
+    def _err(self, st, what):
+        if st != SHT_OK:
+            extra = load().sht_batch_last_error(self._h).decode()
+            msg = what + ": " + load().sht_status_string(st).decode() + (": " + extra if extra else "")
+            if st == SHT_EINVAL:
+                raise ValueError(msg)
+            raise ShtError(st, msg)
+
+    def set_tuning(self, knob: int, value: int):
+        self._err(load().sht_batch_set_tuning(self._h, int(knob), int(value)), "sht_batch_set_tuning")
+
+    def tuning(self, knob: int) -> int:
+        return int(load().sht_batch_tuning(self._h, int(knob)))
+
+    def run(self, stream=None):
+        self._err(load().sht_batch_run(self._h, _stream_ptr(stream)), "sht_batch_run")
+
+    def tiles(self, stage: int) -> int:
+        return int(load().sht_batch_tiles(self._h, int(stage)))
+
+    def close(self):
+        if self._h:
+            load().sht_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
