@@ -15,6 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsht.so")
+LIBDIR_CHECK = os.path.join(HERE, "_lib_check")
 SOURCES = ["sht_plan.cu", "legendre.cu", "legendre_tc.cu", "legendre_df.cu", "ringfft.cu", "diag.cu", "noalloc.cu", "spin.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -31,24 +32,29 @@ def _flags():
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "sht.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build _lib/libsht.so; with checked=True the bounds-checked variant (nvcc -DSHT_CHECK:
+    out-of-bounds kernel accesses are skipped and reported in bit 1 of the plan status word)
+    into _lib_check/libsht.so instead."""
+    libdir = LIBDIR_CHECK if checked else LIBDIR
+    lib = os.path.join(libdir, "libsht.so")
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(libdir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(libdir, os.path.splitext(src)[0] + ".o")
+        cmd = [cc] + _flags() + (["-DSHT_CHECK"] if checked else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,13 +67,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose and err:
                 print(err)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

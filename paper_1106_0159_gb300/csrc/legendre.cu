@@ -223,8 +223,10 @@ __device__ __forceinline__ void synth_body(const SynArgs &A, int m, int blk, Coe
 #pragma unroll
         for (int g = 0; g < NM; ++g) {
             double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-            if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(Er[g] + Or[g], Ei[g] + Oi[g]);
-            if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(Er[g] - Or[g], Ei[g] - Oi[g]);
+            if (rn >= 0 && SHT_CHK(rn < A.nrings && m <= A.mmax))
+                d[(int64_t)rn * mstride + m] = make_double2(Er[g] + Or[g], Ei[g] + Oi[g]);
+            if (rs >= 0 && SHT_CHK(rs < A.nrings && m <= A.mmax))
+                d[(int64_t)rs * mstride + m] = make_double2(Er[g] - Or[g], Ei[g] - Oi[g]);
         }
     }
 }
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(SYN_T) legendre_synth_kernel(SynArgs A)
             const int64_t mstride = A.mmax + 1;
             for (int g = 0; g < NM; ++g) {
                 double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-                if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
-                if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
+                if (rn >= 0 && SHT_CHK(rn < A.nrings)) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
+                if (rs >= 0 && SHT_CHK(rs < A.nrings)) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
             }
         }
         return;
@@ -433,7 +435,8 @@ __device__ __forceinline__ void anal_body(const AnaArgs &A, int m, int blk, Coef
                 re /= c;
                 im /= c;
             }
-            A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + ix] = make_double2(re, im);
+            if (SHT_CHK(ix >= 0 && ix < A.nalm && blk < A.nblk))
+                A.partial[(int64_t)blk * A.part_blk_stride + (int64_t)g * A.part_map_stride + ix] = make_double2(re, im);
         }
     }
 }
@@ -842,5 +845,10 @@ cudaError_t launch_block_reduce(const Plan &p, const double2 *partial, double2 *
                                                 (int64_t)nmaps * p.nalm);
     return cudaGetLastError();
 }
+
+namespace {
+SHT_CHECK_TAKE_DEF(take_check)
+}  // namespace
+cudaError_t take_check_word_legendre(int *w) { return take_check(w); }
 
 }  // namespace sht

@@ -433,8 +433,10 @@ __global__ void __launch_bounds__(DFS_T) synth_df_polar_kernel(DfSynArgs A)
             const double er = widen_df(acc[0][g][0]), ei = widen_df(acc[0][g][1]);
             const double orr = widen_df(acc[1][g][0]), oi = widen_df(acc[1][g][1]);
             double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-            if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
-            if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
+            if (rn >= 0 && SHT_CHK(rn < A.nrings && m <= A.mmax))
+                d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
+            if (rs >= 0 && SHT_CHK(rs < A.nrings && m <= A.mmax))
+                d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
         }
     }
 }
@@ -614,5 +616,10 @@ cudaError_t launch_legendre_anal_df(const Plan &p, const double2 *delta, double2
     ++*nlaunch;
     return e;
 }
+
+namespace {
+SHT_CHECK_TAKE_DEF(take_check)
+}  // namespace
+cudaError_t take_check_word_df(int *w) { return take_check(w); }
 
 }  // namespace sht

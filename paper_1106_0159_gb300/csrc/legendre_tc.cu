@@ -569,8 +569,8 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
             const int64_t mstride = A.mmax + 1;
             for (int g = 0; g < A.nmaps; ++g) {
                 double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-                if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
-                if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
+                if (rn >= 0 && SHT_CHK(rn < A.nrings)) d[(int64_t)rn * mstride + m] = make_double2(0.0, 0.0);
+                if (rs >= 0 && SHT_CHK(rs < A.nrings)) d[(int64_t)rs * mstride + m] = make_double2(0.0, 0.0);
             }
         }
         return;
@@ -724,8 +724,10 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
                         const double er = acc[0][2 * gg] * sr, ei = acc[0][2 * gg + 1] * si;
                         const double orr = acc[1][2 * gg] * sr, oi = acc[1][2 * gg + 1] * si;
                         double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-                        if (rn >= 0) d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
-                        if (rs >= 0) d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
+                        if (rn >= 0 && SHT_CHK(rn < A.nrings && m <= A.mmax))
+                            d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
+                        if (rs >= 0 && SHT_CHK(rs < A.nrings && m <= A.mmax))
+                            d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
                     }
                 }
             }
@@ -984,8 +986,8 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                 double2 dn = make_double2(0.0, 0.0), ds = make_double2(0.0, 0.0);
                 if (g < nm) {
                     const double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
-                    if (rn >= 0) dn = d[(int64_t)rn * mstride + m];
-                    if (rs >= 0) ds = d[(int64_t)rs * mstride + m];
+                    if (rn >= 0 && SHT_CHK(rn < A.nrings)) dn = d[(int64_t)rn * mstride + m];
+                    if (rs >= 0 && SHT_CHK(rs < A.nrings)) ds = d[(int64_t)rs * mstride + m];
                 }
                 xv[0][gg][0] = dn.x + ds.x;
                 xv[0][gg][1] = dn.y + ds.y;
@@ -1095,7 +1097,7 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                 for (int t = 0; t < 16; ++t) {
                     const float2 v = df_sum(acc[t], xch[t * TA_R + erow]);
                     const int l = l0 + 2 * t + es;
-                    if (l <= L) {
+                    if (l <= L && SHT_CHK(base + (l - m) >= A.idx0 && base + (l - m) < A.idx0 + A.nalm_part)) {
                         float2 *dst = reinterpret_cast<float2 *>(part + (base + (l - m)) * nm + eg) + ec;
                         *dst = make_float2(v.x * sc, v.y * sc);
                     }
@@ -1355,5 +1357,10 @@ cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 
     }
     return cudaSuccess;
 }
+
+namespace {
+SHT_CHECK_TAKE_DEF(take_check)
+}  // namespace
+cudaError_t take_check_word_tc(int *w) { return take_check(w); }
 
 }  // namespace sht

@@ -6,6 +6,8 @@
 // every translation unit keeps its own internal copy.
 #pragma once
 
+#include "check.cuh"
+
 constexpr int RESCALE_THR = 1023 + 256;  // biased exponent of y that triggers a rescale by 2^-512
 constexpr double POLAR_SIN = 0.03;       // slot blocks starting below this sin(theta) use the Reinsch form
 

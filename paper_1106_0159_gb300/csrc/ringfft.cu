@@ -36,6 +36,8 @@ namespace {
 #define RING_CTAS_PER_SM 2
 #endif
 constexpr int FFT_T = RING_T;
+
+#include "check.cuh"
 constexpr int MAXR = 13;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
@@ -312,6 +314,9 @@ __device__ void ring_synth_unit(const RingArgs<P> &A, int item, int g, typename 
     const FftItem it = A.items[item];
     const FftLen &F = A.lens[it.len_id];
     const int n = it.n;
+    if (!SHT_CHK(it.ringA >= 0 && it.ringA < A.nrings && it.ringB < A.nrings && n <= A.maxlen && F.M <= A.maxlen &&
+                 A.ofs[it.ringA] + n <= A.npix && (it.ringB < 0 || A.ofs[it.ringB] + n <= A.npix)))
+        return;
     const double2 *dA = A.delta_in + ((int64_t)g * A.nrings + it.ringA) * mstride;
     const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
     const double2 *dB = it.ringB >= 0 ? A.delta_in + ((int64_t)g * A.nrings + it.ringB) * mstride : nullptr;
@@ -360,6 +365,9 @@ __device__ void ring_anal_unit(const RingArgs<P> &A, int item, int g, typename P
     const FftItem it = A.items[item];
     const FftLen &F = A.lens[it.len_id];
     const int n = it.n;
+    if (!SHT_CHK(it.ringA >= 0 && it.ringA < A.nrings && it.ringB < A.nrings && n <= A.maxlen && F.M <= A.maxlen &&
+                 A.ofs[it.ringA] + n <= A.npix && (it.ringB < 0 || A.ofs[it.ringB] + n <= A.npix)))
+        return;
     const double *sA = A.map_in + (int64_t)g * A.npix + A.ofs[it.ringA];
     const double *sB = it.ringB >= 0 ? A.map_in + (int64_t)g * A.npix + A.ofs[it.ringB] : nullptr;
     for (int j = threadIdx.x; j < n; j += blockDim.x)
@@ -825,5 +833,10 @@ cudaError_t batch_ring_launch(const BatchLaunch &L, bool synth, double2 *scratch
                                                               maxlen, scratch, counter);
     return cudaGetLastError();
 }
+
+namespace {
+SHT_CHECK_TAKE_DEF(take_check)
+}  // namespace
+cudaError_t take_check_word_ring(int *w) { return take_check(w); }
 
 }  // namespace sht

@@ -224,6 +224,13 @@ cudaError_t batch_ring_setup(const std::vector<const Plan *> &plans, const std::
 cudaError_t batch_ring_launch(const BatchLaunch &L, bool synth, double2 *scratch, int maxlen, int *counter, int grid,
                               cudaStream_t st);
 
+// bounds-check words of the checked build (bit 1; always 0 in the normal build): read and cleared
+cudaError_t take_check_word_legendre(int *w);
+cudaError_t take_check_word_df(int *w);
+cudaError_t take_check_word_tc(int *w);
+cudaError_t take_check_word_spin(int *w);
+cudaError_t take_check_word_ring(int *w);
+
 cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *map, double2 *scratch, int nmaps,
                                    int grid, cudaStream_t st);
 

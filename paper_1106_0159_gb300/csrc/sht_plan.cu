@@ -482,6 +482,14 @@ sht_status sht_plan_device_status(sht_plan_t plan, int *status, int clear)
     // wait for the whole device first, so that no kernel can set the bit after the read
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    // checked build: fold the kernels' bounds-check words into bit 1 (they are process-wide)
+    int w = 0;
+    if (e == cudaSuccess) e = sht::take_check_word_legendre(&w);
+    if (e == cudaSuccess) e = sht::take_check_word_df(&w);
+    if (e == cudaSuccess) e = sht::take_check_word_tc(&w);
+    if (e == cudaSuccess) e = sht::take_check_word_spin(&w);
+    if (e == cudaSuccess) e = sht::take_check_word_ring(&w);
+    if (e == cudaSuccess) *status |= w;
     if (e == cudaSuccess && clear) e = cudaMemset(p.d_status, 0, sizeof(int));
     if (e == cudaSuccess && clear) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(p, e, "device status");

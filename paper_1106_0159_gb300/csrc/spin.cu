@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(SP_T) spin_synth_kernel(SpinArgs A)
         for (int g = 0; g < NM; ++g) {
             double2 *dq = A.delta + (int64_t)(2 * g) * A.nrings * mstride;
             double2 *du = A.delta + (int64_t)(2 * g + 1) * A.nrings * mstride;
-            if (rn >= 0) {
+            if (rn >= 0 && SHT_CHK(rn < A.nrings && m <= A.mmax)) {
                 dq[(int64_t)rn * mstride + m] = make_double2(QPr[g] + QMr[g], QPi[g] + QMi[g]);
                 du[(int64_t)rn * mstride + m] = make_double2(UPr[g] + UMr[g], UPi[g] + UMi[g]);
             }
-            if (rs >= 0) {
+            if (rs >= 0 && SHT_CHK(rs < A.nrings && m <= A.mmax)) {
                 dq[(int64_t)rs * mstride + m] = make_double2(QPr[g] - QMr[g], QPi[g] - QMi[g]);
                 du[(int64_t)rs * mstride + m] = make_double2(UPr[g] - UMr[g], UPi[g] - UMi[g]);
             }
@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(SP_T) spin_anal_kernel(SpinArgs A)
             const double2 *dq = A.delta + (int64_t)(2 * g) * A.nrings * mstride;
             const double2 *du = A.delta + (int64_t)(2 * g + 1) * A.nrings * mstride;
             double2 qn = make_double2(0.0, 0.0), qs = qn, un = qn, us = qn;
-            if (rn >= 0) {
+            if (rn >= 0 && SHT_CHK(rn < A.nrings)) {
                 qn = dq[(int64_t)rn * mstride + m];
                 un = du[(int64_t)rn * mstride + m];
             }
-            if (rs >= 0) {
+            if (rs >= 0 && SHT_CHK(rs < A.nrings)) {
                 qs = dq[(int64_t)rs * mstride + m];
                 us = du[(int64_t)rs * mstride + m];
             }
@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(SP_T) spin_anal_kernel(SpinArgs A)
                 for (int c = 0; c < 4; ++c) t[c] += s_red[w][j][4 * g + c];
             const double hc = 0.5 * s_t[j].w;
             const int64_t ix = base + (c0 - m) + j;
+            if (!SHT_CHK(ix < A.nalm)) continue;
             part[(int64_t)(2 * g) * A.nalm + ix] = make_double2(-hc * t[0], -hc * t[1]);
             part[(int64_t)(2 * g + 1) * A.nalm + ix] = make_double2(hc * t[2], hc * t[3]);
         }
@@ -500,5 +501,10 @@ cudaError_t launch_spin_anal(const Plan &p, const double2 *delta, double2 *alm, 
     }
     return cudaSuccess;
 }
+
+namespace {
+SHT_CHECK_TAKE_DEF(take_check)
+}  // namespace
+cudaError_t take_check_word_spin(int *w) { return take_check(w); }
 
 }  // namespace sht

@@ -24,7 +24,18 @@ def test_every_allocation_failure_is_enomem_without_leak():
     from paper_1106_0159_gb300 import sht
     geom = sht.healpix_geometry(16)
     L = 32
-    sht.Plan(geom, L, L).close()  # context, modules and kernel attributes in place
+    # every kernel used below runs once first: loading a kernel's module on its first launch
+    # reserves device memory of its own, which is not the library's
+    w = sht.Plan(geom, L, L)
+    a0 = torch.from_numpy(inputs.gaussian_alm(L, L, seed=4)).cuda()
+    w.map2alm(w.alm2map(a0))
+    w.set_mode(sht.MODE_SPLIT_BF16)
+    w.map2alm(w.alm2map(a0))
+    w.set_mode(sht.MODE_FP64)
+    w.alm2map_spin(torch.zeros((1, 2, w.nalm), dtype=torch.complex128, device="cuda"))
+    w.close()
+    del a0
+    torch.cuda.synchronize()
     base = _free()
     k = 0
     while True:
