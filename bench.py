@@ -397,28 +397,30 @@ def ours_arm(a, rank, world, local_rank):
         anal = ka_ms >= ks_ms
         ms, nl = (ka_ms, ka_n) if anal else (ks_ms, ks_n)
         key = "tc_anal_kernel" if anal else "tc_synth_kernel"
-        per_launch_s = ms * 1e-3 / nl
-        maps_per_launch = min(B, 16)
+        groups = -(-B // 16) * steps            # passes of the recurrence: one per group of <= 16 maps
+        per_group_s = ms * 1e-3 / groups         # the analysis runs a group as about eight m-slab launches
+        maps_per_group = min(B, 16)
         # binding pipe: the tensor cores.  Useful work = the 28 digit-pair slice-products, each the
         # whole contraction of 4 flops per (l, m, ring-pair) step and map (complex x real), over the
         # full triangle S
-        tflops = 28 * 4.0 * maps_per_launch * S / per_launch_s / 1e12
+        tflops = 28 * 4.0 * maps_per_group * S / per_group_s / 1e12
         tpeak = MEASURED.get("bf16_tflops_sustained") or 1725.1
-        # the FP64 recurrence beside it: 3 flops per step, once per launch
-        fflops = 3.0 * S / per_launch_s / 1e12
-        # algorithmic bytes per launch: Delta read and a_lm written (analysis), a_lm read and
+        # the FP64 recurrence beside it: 3 flops per step, once per group
+        fflops = 3.0 * S / per_group_s / 1e12
+        # algorithmic bytes per group: Delta read and a_lm written (analysis), a_lm read and
         # Delta written (synthesis)
-        alg = maps_per_launch * (plan.nrings * (L + 1) + nalm) * 16
+        alg = maps_per_group * (plan.nrings * (L + 1) + nalm) * 16
         traffic = traffic_from_profiles(key)
         return {"bound": "tensor", "kernel": key, "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": tflops / tpeak, "traffic": traffic,
                 "peak_source": "measured bf16 GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained): the "
                                "kernel is timed inside a long step",
                 "work": "28 bf16 digit-pair products x 4 flops per (l, m, ring-pair) step and map, nominal full "
-                        "triangle S = %d steps, %d maps per launch: %.3e flops per launch" %
-                        (S, maps_per_launch, 28 * 4.0 * maps_per_launch * S),
+                        "triangle S = %d steps, %d maps per group: %.3e flops per group" %
+                        (S, maps_per_group, 28 * 4.0 * maps_per_group * S),
                 "time": "the kernel's own launches (CUDA events around each launch on the call's stream): "
-                        "%.2f ms per launch, %d launches" % (per_launch_s * 1e3, nl),
+                        "%.2f ms per group of %d maps, %d launches in %d groups" %
+                        (per_group_s * 1e3, maps_per_group, nl, groups),
                 "live_share": live_share,
                 "frac_of_executed": tflops / tpeak / live_share,
                 "fp64": {"achieved": fflops, "peak": peak_tf, "unit": "TFLOP/s", "frac": fflops / peak_tf,
@@ -790,8 +792,10 @@ def batch_leg(a, rep, local_rank):
             pb = batch.PersistentBatch(jobs)
             t0 = time.perf_counter()
             cache = {}
-            ptuned = {d: autotune.tune_batch(bb, d, cache=cache, key=autotune.batch_key(
-                [(j.plan, j.src) for j in jobs if j.direction == d], d)) for d, bb in pb.batches}
+            ptuned = {d: autotune.tune_batch(bb, d, cache=cache, passes=1, timer=functools.partial(
+                autotune.batch_timer, reps=1), key=autotune.batch_key([(j.plan, j.src) for j in jobs
+                                                                       if j.direction == d], d))
+                      for d, bb in pb.batches}
             ptune_s = time.perf_counter() - t0
             pb.capture()
             p_ms = timed(pb.replay)

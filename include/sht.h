@@ -268,7 +268,7 @@ typedef enum {
     SHT_BATCH_LEG_CTAS = 1,    /* persistent Legendre CTAs per SM: 2, 4, 8 or 16 (default 8) */
     SHT_BATCH_RING_CTAS = 2,   /* persistent ring CTAs per SM: 1 to 4 (default 4) */
     SHT_BATCH_ANAL_MAPS = 3,   /* maps per Legendre analysis tile: 1 or 2 (default 2) */
-    SHT_BATCH_ANAL_SLOTS = 4,  /* ring slots per thread of the analysis tiles: 1 or 4 (default 1) */
+    SHT_BATCH_ANAL_SLOTS = 4,  /* ring slots per thread of the analysis tiles: 1 or 4 (default 4) */
     SHT_BATCH_TUNE_COUNT = 5
 } sht_batch_tune;
 sht_status  sht_batch_create(sht_batch_t *out, int direction /* 0 alm2map, 1 map2alm */, int njobs,

@@ -166,10 +166,10 @@ def batch_timer(batch, reps: int = 2) -> float:
 
 
 def tune_batch(batch, direction: str, timer: Callable = batch_timer, cache: Optional[Dict[str, dict]] = None,
-               key: Optional[str] = None) -> dict:
+               key: Optional[str] = None, passes: int = 2) -> dict:
     """Coordinate search over the batch knobs: from the defaults, each knob in turn takes the
-    fastest of its values with the others fixed, twice over.  Returns {"knobs", "ms", "default_ms",
-    "tried"}; with a cache and a key, a cached record is applied without timing."""
+    fastest of its values with the others fixed, `passes` times over.  Returns {"knobs", "ms",
+    "default_ms", "tried"}; with a cache and a key, a cached record is applied without timing."""
     if cache is not None and key is not None and key in cache:
         for k, v in cache[key]["knobs"].items():
             batch.set_tuning(int(k), int(v))
@@ -179,7 +179,7 @@ def tune_batch(batch, direction: str, timer: Callable = batch_timer, cache: Opti
     default_ms = float(timer(batch))
     best_ms = default_ms
     tried = []
-    for _ in range(2):
+    for _ in range(max(1, passes)):
         for k in ks:
             for v in sht.BATCH_TUNE_VALUES[k]:
                 if v == cur[k]:

@@ -19,7 +19,7 @@ struct sht_batch_s {
     std::vector<int> nmaps;
     std::vector<const void *> in;
     std::vector<void *> out;
-    int tune[SHT_BATCH_TUNE_COUNT] = {4, 8, 4, 2, 1};
+    int tune[SHT_BATCH_TUNE_COUNT] = {4, 8, 4, 2, 4};
     // device state, rebuilt when a knob changes
     void *d_ws = nullptr;                    // Delta slabs, then partial sums / ring scratch
     size_t ws_bytes = 0;

@@ -65,9 +65,7 @@ static_assert(TC_S >= 6 && TC_S <= 7, "the digit split needs 53 - (7 S - 1) >= 1
 constexpr int TC_CH = 32;           // l per chunk: 16 even + 16 odd
 constexpr int TC_ATILE = 128 * 16 * 2;  // bytes of one [128 x 16] bf16 tile
 constexpr long long WAIT_POLLS = 1ll << 26;
-#ifndef TC_NACC
-#define TC_NACC 5       // accumulators per parity: classes 0 .. TC_NACC-2 alone, the rest together
-#endif
+constexpr int TC_NCLS = 8;  // synthesis accumulator blocks per parity: digit classes 0 .. 7, one each
 #ifndef TC_MAXW
 #define TC_MAXW (TC_S - 1)  // highest digit class i + j accumulated
 #endif
@@ -196,13 +194,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
     return false;
 }
 
+// Synthesis operands.  B stacks two a_lm digits along N: stack sb = [B_(2 sb) | B_(2 sb + 1)]
+// (N2 = 2N columns, digit 7 zero), so one MMA A_a x stack b/2 adds class a + b to accumulator block
+// a + b and class a + b + 1 to block a + b + 1: the accumulators of a parity are one run of 8 blocks
+// of N columns, block c holding class c only.
 template <int N>
 struct TcTile {
-    static constexpr int B_TILE = N * 16 * 2;                 // bytes of one [N x 16] tile
-    static constexpr int B_CHUNK = 2 * TC_S * B_TILE;         // a_lm digits of one chunk
+    static constexpr int N2 = 2 * N;                          // columns of one B stack
+    static constexpr int B_TILE = N2 * 16 * 2;                // bytes of one [N2 x 16] stack
+    static constexpr int NSTK = (TC_S + 1) / 2;               // stacks per parity
+    static constexpr int B_CHUNK = 2 * NSTK * B_TILE;         // a_lm digits of one chunk
     static constexpr int A_BYTES = 2 * TC_S * TC_ATILE;
-    static constexpr int NACC = TC_NACC;                      // accumulators per parity
-    static constexpr int TMEM_COLS = (2 * NACC * N <= 128) ? 128 : (2 * NACC * N <= 256) ? 256 : 512;
+    static constexpr int TMEM_COLS = (2 * TC_NCLS * N <= 128) ? 128 : (2 * TC_NCLS * N <= 256) ? 256 : 512;
 };
 
 struct TcArgs {
@@ -266,7 +269,8 @@ __global__ void tc_scale_kernel(TcArgs A)
 }
 
 // digits of c_lm a_lm for one (m, chunk) in the tile layout of the MMA B operand:
-// [parity][digit][N x 16] bf16, core matrix (n/8, k/8) at ((k/8) (N/8) + n/8) * 64 elements
+// [parity][stack][N2 x 16] bf16 with digit s in stack s / 2 at columns n + N (s & 1), core matrix
+// (n2/8, k/8) at ((k/8) (N2/8) + n2/8) * 64 elements; digit 7 is zero
 template <int N>
 __global__ void tc_split_b_kernel(TcArgs A)
 {
@@ -289,9 +293,13 @@ __global__ void tc_split_b_kernel(TcArgs A)
         }
         float d[TC_S];
         split_digits(v, A.Ea[m * N + n], d);
-        const int off = ((k >> 3) * (N / 8) + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+        constexpr int N2 = TcTile<N>::N2;
 #pragma unroll
-        for (int s = 0; s < TC_S; ++s) out[(eo * TC_S + s) * (N * 16) + off] = __float2bfloat16_rn(d[s]);
+        for (int s = 0; s < 2 * TcTile<N>::NSTK; ++s) {
+            const int n2 = n + N * (s & 1);
+            const int off = ((k >> 3) * (N2 / 8) + (n2 >> 3)) * 64 + (n2 & 7) * 8 + (k & 7);
+            out[(eo * TcTile<N>::NSTK + (s >> 1)) * (N2 * 16) + off] = __float2bfloat16_rn(s < TC_S ? d[s] : 0.f);
+        }
     }
 }
 
@@ -598,13 +606,12 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
         recurrence_warps<TC_T>(A, m, blk, r, active, base, nch, cfirst, ybuf);
     } else if (issuer) {
         // ------------------------------------------------ MMA issue (one lane of the last warp)
-        // per chunk: wait until the stage's tiles are written, issue its 2 x 28 MMAs (per parity eo,
-        // classes 0 .. NACC - 2 alone and the rest merged, each accumulator's MMAs in order) and
-        // commit them to the stage's done barrier.  The whole warp runs the loop with warp-uniform
+        // per chunk: wait until the stage's tiles are written, issue its 2 x 16 MMAs (per parity eo,
+        // A digit a against B stack b/2 for a + b <= 6) and commit them to the stage's done barrier.  The whole warp runs the loop with warp-uniform
         // descriptors; one elected lane issues.
-        const uint32_t idesc = umma_idesc<N>();
+        const uint32_t idesc = umma_idesc<TcTile<N>::N2>();
         const uint64_t dA0 = umma_desc(smem_u32(sA), 16 * 128, 128);
-        const uint64_t dB0 = umma_desc(smem_u32(sB), (N / 8) * 128, 128);
+        const uint64_t dB0 = umma_desc(smem_u32(sB), (TcTile<N>::N2 / 8) * 128, 128);
         const uint32_t issue = elect_one();
         for (int q = 0; q < nlive; ++q) {
             const int st = q & 1;
@@ -617,15 +624,16 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo) {
 #pragma unroll
-                for (int w = 0; w <= TC_MAXW; ++w) {
+                for (int a = 0; a < TC_S; ++a) {
 #pragma unroll
-                    for (int i = 0; i <= w; ++i) {
-                        const int j = w - i;
-                        const int cls = w < TcTile<N>::NACC - 1 ? w : TcTile<N>::NACC - 1;
-                        const bool first = (q == 0) && (i == 0) && (w <= TcTile<N>::NACC - 1);
-                        umma_bf16_by(issue, tmem + (uint32_t)((eo * TcTile<N>::NACC + cls) * N),
-                                     aS + (uint64_t)(((eo * TC_S + i) * TC_ATILE) >> 4),
-                                     bS + (uint64_t)(((eo * TC_S + j) * TcTile<N>::B_TILE) >> 4), idesc, first ? 0u : 1u);
+                    for (int b = 0; b + a <= TC_MAXW; b += 2) {
+                        // classes a + b and a + b + 1 into blocks a + b, a + b + 1; the a = 0 MMAs of the
+                        // first live chunk write blocks 0-7 once each, so they start the sums
+                        const bool first = (q == 0) && (a == 0);
+                        umma_bf16_by(issue, tmem + (uint32_t)((eo * TC_NCLS + a + b) * N),
+                                     aS + (uint64_t)(((eo * TC_S + a) * TC_ATILE) >> 4),
+                                     bS + (uint64_t)(((eo * TcTile<N>::NSTK + b / 2) * TcTile<N>::B_TILE) >> 4), idesc,
+                                     first ? 0u : 1u);
                     }
                 }
             }
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
         ok = bar_red_and(BAR_SPLIT, NS, ok);
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {
-            // accumulators: column (eo * NACC + cls) * N + n, lane = slot within the block; this thread
+            // accumulators: column (eo * 8 + class) * N + n, lane = slot within the block; this thread
             // takes columns [par N/2, (par + 1) N/2)
             constexpr int NH = N / 2;
             const int lw = warp & 3;  // this warp may read lanes 32 lw .. 32 lw + 31
@@ -696,12 +704,12 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo) {
 #pragma unroll
-                for (int cls = 0; cls < TcTile<N>::NACC; ++cls) {
+                for (int cls = 0; cls < TC_NCLS; ++cls) {
 #pragma unroll
                     for (int n0 = 0; n0 < NH; n0 += 8) {
                         uint32_t v[8];
                         const uint32_t addr = tmem + ((uint32_t)(lw * 32) << 16) +
-                                              (uint32_t)((eo * TcTile<N>::NACC + cls) * N + par * NH + n0);
+                                              (uint32_t)((eo * TC_NCLS + cls) * N + par * NH + n0);
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
                                        "=r"(v[6]), "=r"(v[7])
@@ -1309,7 +1317,7 @@ size_t tc_workspace_bytes(const Plan &p, int nmaps)
 {
     if (nmaps <= 0) return 0;
     const int n = std::min(nmaps, p.tune[SHT_TUNE_TC_MAPS]) > 8 ? 32 : 16;
-    const size_t bchunk = (size_t)2 * TC_S * n * 16 * 2;
+    const size_t bchunk = n > 16 ? (size_t)TcTile<32>::B_CHUNK : (size_t)TcTile<16>::B_CHUNK;
     return (size_t)p.tc_total_chunks * bchunk + (size_t)(p.mmax + 1) * 32 * sizeof(int) + 256;
 }
 
@@ -1347,7 +1355,7 @@ cudaError_t launch_legendre_synth_tc(const Plan &p, const double2 *alm, double2 
         A.alm = alm + (int64_t)g0 * p.nalm;
         A.delta = delta + (int64_t)g0 * dstride;
         const int N = nm > 8 ? 32 : 16;
-        const size_t bchunk = (size_t)2 * TC_S * N * 16 * 2;
+        const size_t bchunk = N == 32 ? (size_t)TcTile<32>::B_CHUNK : (size_t)TcTile<16>::B_CHUNK;
         A.bdig = (uint4 *)scratch;
         A.Ea = (int *)((char *)scratch + (size_t)p.tc_total_chunks * bchunk);
         cudaError_t e = (N == 32) ? launch_group<32>(p, A, st) : launch_group<16>(p, A, st);

@@ -102,3 +102,44 @@ def test_streams_keep_a_plans_jobs_together_and_balance_work():
         GraphBatch([Job(a, "sideways", Arr(1), None)])
     with pytest.raises(RuntimeError):
         GraphBatch(jobs).replay()
+
+
+class _FakeBatch:
+    """Stands in for sht.Batch: knob values and a cost surface with one best point."""
+
+    def __init__(self, best):
+        from paper_1106_0159_gb300 import sht
+        self.k = {sht.BATCH_SYNTH_MAPS: 4, sht.BATCH_LEG_CTAS: 8, sht.BATCH_RING_CTAS: 4, sht.BATCH_ANAL_MAPS: 2,
+                  sht.BATCH_ANAL_SLOTS: 4}
+        self.best = best
+        self.sets = 0
+
+    def tuning(self, knob):
+        return self.k[knob]
+
+    def set_tuning(self, knob, value):
+        from paper_1106_0159_gb300 import sht
+        assert value in sht.BATCH_TUNE_VALUES[knob]
+        self.k[knob] = value
+        self.sets += 1
+
+    def cost(self):
+        return 10.0 + sum(abs(self.k[k] - v) for k, v in self.best.items())
+
+
+def test_tune_batch_finds_the_best_tile_shapes_and_grids():
+    from paper_1106_0159_gb300 import sht
+    best = {sht.BATCH_SYNTH_MAPS: 2, sht.BATCH_LEG_CTAS: 16, sht.BATCH_RING_CTAS: 2}
+    b = _FakeBatch(best)
+    rec = autotune.tune_batch(b, autotune.ALM2MAP, timer=lambda bb: bb.cost())
+    assert rec["ms"] == 10.0 and rec["default_ms"] > 10.0
+    assert {int(k): v for k, v in rec["knobs"].items()} == best
+    assert all(b.k[k] == v for k, v in best.items())          # left at the best setting
+    cache = {}
+    b2 = _FakeBatch(best)
+    autotune.tune_batch(b2, autotune.ALM2MAP, timer=lambda bb: bb.cost(), cache=cache, key="k")
+    b3 = _FakeBatch(best)
+    again = autotune.tune_batch(b3, autotune.ALM2MAP, timer=lambda bb: 1e9, cache=cache, key="k")
+    assert again is cache["k"] and all(b3.k[k] == v for k, v in best.items())   # cached: applied, not timed
+    assert autotune.batch_knobs(autotune.MAP2ALM) == [sht.BATCH_ANAL_MAPS, sht.BATCH_ANAL_SLOTS, sht.BATCH_LEG_CTAS,
+                                                      sht.BATCH_RING_CTAS]

@@ -27,7 +27,7 @@ def setup():
     from paper_1106_0159_gb300 import sht
     plans = {L: sht.Plan(sht.healpix_geometry(L // 2), L, L, grid=sht.GRID_HEALPIX) for L in LMAXES}
     for p in plans.values():
-        p.set_tuning(sht.TUNE_ANAL_SLOTS, 1)   # the batch's default slots per thread
+        p.set_tuning(sht.TUNE_ANAL_SLOTS, 4)   # the batch's default slots per thread
     syn, ana = [], []
     for L in LMAXES:
         p = plans[L]
