@@ -240,7 +240,11 @@ typedef enum {
     SHT_TUNE_TC_MAPS = 4,    /* precision-form synthesis: maps per tensor-core launch, 8 or 16 (default 16) */
     SHT_TUNE_PREC_ANAL = 5,  /* precision-form analysis kernel: 0 double-float FP32, 1 tensor cores (default) */
     SHT_TUNE_PREC_RING = 6,  /* precision-form ring DFTs: 1 double-float FP32 (default), 0 FP64 */
-    SHT_TUNE_COUNT = 7
+    SHT_TUNE_RING_SMEM = 7,  /* ring DFTs: 1 in shared memory where the ring fits, 0 all through the
+                                global scratch, 2 (default) shared memory for the FP64 DFTs and the
+                                global scratch for the precision form's double-float DFTs; results
+                                agree to rounding */
+    SHT_TUNE_COUNT = 8
 } sht_tune;
 sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value);
 int sht_plan_tuning(sht_plan_t plan, int knob); /* the knob's value; -1 for a null plan or unknown knob */

@@ -42,6 +42,20 @@ struct FftLen {
     int64_t tw;       // offset of exp(2 pi i k / n), k < n   (smooth) or of exp(2 pi i k / M), k < M (Bluestein)
     int64_t chirp;    // offset of exp(i pi j^2 / n), j < n   (Bluestein)
     int64_t filt;     // offset of FFT_M(h) / M, M entries      (Bluestein)
+    // Shared-memory path (sm != 0; ringfft.cu): in-place DIF stages with radices rad[0 .. nst-1] over
+    // the data in shared memory leave the spectrum in digit-reversed order, bin k at position
+    // perm[k].  split != 0: stage 0 (radix p = rad[0], not smooth) runs as Bluestein DFTs of length p
+    // in a second shared buffer, bat at a time: forward DIF of length Mb (radices brad), the filter
+    // multiplied in the DIF output order, DIT back to natural order.
+    int sm, nst, rad[16];
+    int split, Mb, nbr, brad[16], bat;
+    int64_t tw_n;     // exp(2 pi i k / n), k < n
+    int64_t perm;     // offset into the int table: perm[k], k < n
+    int64_t chirp_p;  // exp(i pi j^2 / p), j < p
+    int64_t tw_M;     // exp(2 pi i k / Mb), k < Mb
+    int64_t filt_M;   // filter of length Mb in DIF output order
+    int smem_entries; // complex entries of shared memory the path takes: n + bat Mb + twq
+    int twq;          // n / 4 when the quarter-wave table of exp(2 pi i k / n) is staged in shared memory, else 0
 };
 
 struct Plan {
@@ -79,6 +93,9 @@ struct Plan {
     float4 *d_phase_df = nullptr;
     int64_t fft_tab_len = 0;
     int fft_maxlen = 0;         // per-CTA scratch length (complex entries, per buffer)
+    int *d_fft_perm = nullptr;  // spectrum positions of the shared-memory DFTs
+    int ring_smem = 0;          // dynamic shared memory of the ring kernels (bytes), 0: none fit
+    int ring_occ = 1;           // ring CTAs resident per SM with that shared memory
 
     // precision form (split-bf16 contraction on the tensor cores)
     int mode = 0;                       // SHT_MODE_FP64 or SHT_MODE_SPLIT_BF16
@@ -96,7 +113,7 @@ struct Plan {
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
 
     // launch tuning (sht_tune): maps or slots per thread per launch
-    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 1, 1};
+    int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 1, 1, 2};
 
     // workspace, grown on demand
     void *d_ws = nullptr;
@@ -196,6 +213,7 @@ struct BatchLaunch {
     int4 *tiles = nullptr;    // device tile list
     int ntiles = 0;
     int k = 1;                // analysis: ring slots per thread
+    int smem = 0;             // ring DFTs: dynamic shared memory per CTA (bytes)
 };
 struct BatchReduceJob {
     const double2 *partial;

@@ -3,6 +3,8 @@
 // entry points declared in include/sht.h.
 #include "sht_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -43,8 +45,15 @@ static cudaEvent_t pool_event(const Plan &p)
     return e;
 }
 
+// NVTX range names of the stages (sht.h stage ids); the ranges mark where each stage is enqueued
+// (header-only NVTX 3: without an attached tool the calls do nothing)
+static const char *const kStageNames[SHT_NSTAGES] = {"sht legendre_synth", "sht ring_synth", "sht ring_anal",
+                                                     "sht legendre_anal", "sht block_reduce", "sht tc_synth_kernel",
+                                                     "sht tc_anal_kernel"};
+
 StageEvents::StageEvents(const Plan &pl, int st, cudaStream_t str) : p(pl), stage(st), s(str)
 {
+    nvtxRangePushA(kStageNames[st]);
     if (p.timing) {
         a = pool_event(p);
         b = pool_event(p);
@@ -65,6 +74,7 @@ StageEvents::~StageEvents()
 {
     if (a) p.event_pool.push_back(a);
     if (b) p.event_pool.push_back(b);
+    nvtxRangePop();
 }
 
 }  // namespace sht
@@ -88,7 +98,7 @@ void free_plan_device(Plan &p)
     void *ptrs[] = {p.d_slotN, p.d_slotS, p.d_u,     p.d_s,     p.d_alpha,   p.d_cfac,    p.d_ofs, p.d_nphi,
                     p.d_w,     p.d_phase, p.d_items, p.d_lens,  p.d_fft_tab, p.d_rein, p.d_ws,
                     p.d_tc_chunk_base, p.d_tc_chunk_m, p.d_tc_Ey, p.d_status, p.d_fft_tab_df, p.d_phase_df,
-                    p.d_tc_ck_y, p.d_tc_ck_k, p.d_spin_tab, p.d_spin_start, p.d_mflag};
+                    p.d_tc_ck_y, p.d_tc_ck_k, p.d_spin_tab, p.d_spin_start, p.d_mflag, p.d_fft_perm};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p.d_slotN = p.d_slotS = nullptr;
@@ -113,6 +123,7 @@ void free_plan_device(Plan &p)
     p.d_spin_start = nullptr;
     p.d_mflag = nullptr;
     p.n_mlist = 0;
+    p.d_fft_perm = nullptr;
     p.ws_bytes = 0;
 }
 
@@ -438,6 +449,7 @@ sht_status sht_plan_set_tuning(sht_plan_t plan, int knob, int value)
     case SHT_TUNE_TC_MAPS: ok = value == 8 || value == 16; break;
     case SHT_TUNE_PREC_ANAL: ok = value == 0 || value == 1; break;
     case SHT_TUNE_PREC_RING: ok = value == 0 || value == 1; break;
+    case SHT_TUNE_RING_SMEM: ok = value >= 0 && value <= 2; break;
     default: ok = false;
     }
     if (!ok) return SHT_EINVAL;

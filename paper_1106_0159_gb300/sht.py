@@ -43,9 +43,11 @@ EXPORTS = (
 )
 MODE_FP64, MODE_SPLIT_BF16 = 0, 1
 # launch tuning knobs (sht_tune) and the values each takes
-TUNE_SYNTH_MAPS, TUNE_ANAL_MAPS, TUNE_ANAL_SLOTS, TUNE_DF_MAPS, TUNE_TC_MAPS, TUNE_PREC_ANAL, TUNE_PREC_RING = range(7)
+(TUNE_SYNTH_MAPS, TUNE_ANAL_MAPS, TUNE_ANAL_SLOTS, TUNE_DF_MAPS, TUNE_TC_MAPS, TUNE_PREC_ANAL, TUNE_PREC_RING,
+ TUNE_RING_SMEM) = range(8)
 TUNE_VALUES = {TUNE_SYNTH_MAPS: (1, 2, 4), TUNE_ANAL_MAPS: (1, 2), TUNE_ANAL_SLOTS: (1, 4),
-               TUNE_DF_MAPS: (4, 8, 16), TUNE_TC_MAPS: (8, 16), TUNE_PREC_ANAL: (0, 1), TUNE_PREC_RING: (0, 1)}
+               TUNE_DF_MAPS: (4, 8, 16), TUNE_TC_MAPS: (8, 16), TUNE_PREC_ANAL: (0, 1), TUNE_PREC_RING: (0, 1),
+               TUNE_RING_SMEM: (0, 1, 2)}
 STAGES = ("legendre_synth", "ring_synth", "ring_anal", "legendre_anal", "block_reduce", "tc_synth_kernel",
           "tc_anal_kernel")
 

@@ -122,10 +122,12 @@ def _awkward_geometry():
     return nphi, theta, phi0, w
 
 
+@pytest.mark.parametrize("smem", [1, 0])
 @pytest.mark.parametrize("mmax", [0, 5, 40, 300])
-def test_ring_synth_awkward_lengths(mmax):
+def test_ring_synth_awkward_lengths(mmax, smem):
     geom = _awkward_geometry()
     p = plan_for(geom, mmax, mmax)
+    p.set_tuning(_sht().TUNE_RING_SMEM, smem)
     d = inputs.random_delta(len(geom[0]), mmax, seed=16, nmaps=2)
     s = host(p.ring_synth(dev(d)))
     for g in range(2):
@@ -133,16 +135,52 @@ def test_ring_synth_awkward_lengths(mmax):
         assert rel(s[g], ref) < TOL
 
 
+@pytest.mark.parametrize("smem", [1, 0])
 @pytest.mark.parametrize("mmax", [0, 5, 40, 300])
-def test_ring_anal_awkward_lengths(mmax):
+def test_ring_anal_awkward_lengths(mmax, smem):
     geom = _awkward_geometry()
     p = plan_for(geom, mmax, mmax)
+    p.set_tuning(_sht().TUNE_RING_SMEM, smem)
     s = inputs.white_map(geometry.npix(geom), seed=17, nmaps=2)
     d = host(p.ring_anal(dev(s)))
     for g in range(2):
         ref = oracle.delta_anal(geom, s[g], np.arange(mmax + 1)).T
         assert rel(d[g], ref) < TOL
         assert np.all(d[g][:, 0].imag == 0)
+
+
+def _long_awkward_geometry():
+    # long rings of every shared-memory form: smooth (8192, 6000, 3003 = 3 7 11 13), split with
+    # one Bluestein DFT of the non-smooth part at a time (8156 = 4 2039, 4093 prime, 289 = 17^2) or
+    # several (2038 = 2 1019, 4084 = 4 1021, 255 = 15 17), and lengths whose Bluestein buffer does
+    # not fit in shared memory (8193 = 3 2731, 7919 prime): those take the global-scratch DFTs
+    nphi = np.array([8192, 8156, 8193, 7919, 6000, 4093, 4084, 3003, 2038, 289, 255], np.int64)
+    rng = np.random.default_rng(6)
+    theta = np.sort(rng.uniform(0.05, math.pi - 0.05, len(nphi)))
+    theta[-1] = math.pi - theta[0]          # a pair with lengths 8192 and 255
+    phi0 = rng.uniform(0, 2 * math.pi, len(nphi))
+    w = rng.uniform(0.5, 2.0, len(nphi))
+    return nphi, theta, phi0, w
+
+
+@pytest.mark.parametrize("mmax", [100, 2100])
+def test_ring_stages_long_awkward_lengths(mmax):
+    """Shared-memory DFTs (default) and the global-scratch DFTs against the oracle's direct
+    phi sums, and against each other, on long rings of every factor form."""
+    sht = _sht()
+    geom = _long_awkward_geometry()
+    p = plan_for(geom, mmax, mmax)
+    d = inputs.random_delta(len(geom[0]), mmax, seed=26, nmaps=2)
+    s = inputs.white_map(geometry.npix(geom), seed=27, nmaps=2)
+    syn = host(p.ring_synth(dev(d)))
+    ana = host(p.ring_anal(dev(s)))
+    for g in range(2):
+        assert rel(syn[g], oracle.ring_synth(geom, d[g], mmax)) < TOL
+        assert rel(ana[g], oracle.delta_anal(geom, s[g], np.arange(mmax + 1)).T) < TOL
+    p.set_tuning(sht.TUNE_RING_SMEM, 0)
+    assert rel(host(p.ring_synth(dev(d))), syn) < 1e-13
+    assert rel(host(p.ring_anal(dev(s))), ana) < 1e-13
+    assert p.device_status() == 0
 
 
 def test_gauss_legendre_grid_with_prime_lengths():

@@ -184,6 +184,11 @@ def test_split_ring_stages_match_fp64(grid):
     for g in range(3):
         assert rel(m_split[g], m_64[g]) < 1e-12, g
         assert rel(d_split[g], d_64[g]) < 1e-12, g
+    # the double-float DFTs in shared memory (the default takes the global scratch for them) agree
+    p.set_tuning(sht.TUNE_RING_SMEM, 1)
+    assert rel(host(p.ring_synth(d)), m_split) < 1e-13
+    assert rel(host(p.ring_anal(s)), d_split) < 1e-13
+    p.set_tuning(sht.TUNE_RING_SMEM, 2)
     # the FP64 ring DFTs are still there when the knob asks for them
     p.set_tuning(sht.TUNE_PREC_RING, 0)
     assert np.array_equal(host(p.ring_synth(d)), m_64)
