@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--mode", default="split", choices=["split", "fp64"],
                     help="split: tensor-core synthesis + double-float analysis (<= 1e-9); fp64: plain")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
-    ap.add_argument("--serve-requests", type=int, default=200, help="requests in the serving trace (0: no serving leg)")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
     ap.add_argument("--no-c2", dest="c2", action="store_false",
                     help="skip the plain FP64 lmax = 2048 leg (HEALPix 1024 and the Gauss-Legendre round trip)")
