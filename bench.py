@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="split", choices=["split", "fp64"],
-                    help="split: tensor-core synthesis + double-float analysis (<= 1e-9); fp64: plain")
+                    help="split: precision form, tensor-core synthesis and analysis (<= 1e-9); fp64: plain")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
     ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
