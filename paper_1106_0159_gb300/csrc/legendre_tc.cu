@@ -132,6 +132,24 @@ __device__ __forceinline__ void split_digits(double v, int E, float out[TC_S])
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// a + b = s + e exactly (TwoSum), in _rn operations so that nothing is contracted
+__device__ __forceinline__ float2 two_sum_rn(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// float -> double from the bit pattern (integer pipe; an F2F conversion takes an FP64 issue slot):
+// normal floats exactly, zero and subnormals (far below every value kept here) as 0
+__device__ __forceinline__ double widen_f(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    const uint32_t hi = (b & 0x80000000u) | ((ex + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return ex ? __hiloint2double((int)hi, (int)(b << 29)) : 0.0;
+}
+
 // tcgen05 shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride between core
 // matrices along K, sbo = along M/N; version 1.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -694,17 +712,21 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
         if (ok) {
             // accumulators: column (eo * 8 + class) * N + n, lane = slot within the block; this thread
             // takes columns [par N/2, (par + 1) N/2)
+            // The 8 class blocks are added as double-float pairs on the FP32 pipe, smallest class
+            // first, and each sum is widened once (bit operations and one DADD): widening and adding
+            // every block in FP64 took 512 FP64-pipe instructions per thread, about 65K cycles of a
+            // CTA's end during which the SM (one CTA each) could not start the next one.
             constexpr int NH = N / 2;
             const int lw = warp & 3;  // this warp may read lanes 32 lw .. 32 lw + 31
-            double acc[2][NH];
+            float2 fac[2][NH];
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo)
 #pragma unroll
-                for (int n = 0; n < NH; ++n) acc[eo][n] = 0.0;
+                for (int n = 0; n < NH; ++n) fac[eo][n] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int eo = 0; eo < 2; ++eo) {
 #pragma unroll
-                for (int cls = 0; cls < TC_NCLS; ++cls) {
+                for (int cls = TC_NCLS - 1; cls >= 0; --cls) {
 #pragma unroll
                     for (int n0 = 0; n0 < NH; n0 += 8) {
                         uint32_t v[8];
@@ -716,10 +738,18 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
                                      : "r"(addr));
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                        for (int t = 0; t < 8; ++t) acc[eo][n0 + t] += (double)__uint_as_float(v[t]);
+                        for (int t = 0; t < 8; ++t) {
+                            const float2 sm = two_sum_rn(fac[eo][n0 + t].x, __uint_as_float(v[t]));
+                            fac[eo][n0 + t] = make_float2(sm.x, __fadd_rn(fac[eo][n0 + t].y, sm.y));
+                        }
                     }
                 }
             }
+            double acc[2][NH];
+#pragma unroll
+            for (int eo = 0; eo < 2; ++eo)
+#pragma unroll
+                for (int n = 0; n < NH; ++n) acc[eo][n] = widen_f(fac[eo][n].x) + widen_f(fac[eo][n].y);
             if (active) {
                 const int rn = A.slotN[slot], rs = A.slotS[slot];
                 const int64_t mstride = A.mmax + 1;

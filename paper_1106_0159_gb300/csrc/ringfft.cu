@@ -120,9 +120,11 @@ __device__ __forceinline__ float2 dfn_mul(float2 a, float2 b)
     return make_float2(h, e - (h - p));
 }
 // FP64 -> (hi, lo) from the bit pattern, on the integer pipe (an FP64 <-> FP32 conversion takes an
-// FP64 issue slot): hi = sign, exponent and the top 23 fraction bits; lo = the remaining 29 bits,
-// rounded to 24.  Below 2^-74 the remainder would leave the FP32 range: those (rare) values take
-// the conversion instructions, and values below 2^-126 flush to zero.
+// FP64 issue slot, 1/64 of the FP32 rate on this part): hi = sign, exponent and the top 23 fraction
+// bits; lo = the remaining 29 bits, rounded to 24.  Below 2^-74 the remainder would leave the FP32
+// range and is dropped (|v| < 2^-74: an absolute error below 2^-97); below 2^-126 v flushes to zero.
+// Such tiny values are common (the folded Delta_m of a polar ring past its turning point), so they
+// take no conversion instruction either.
 __device__ __forceinline__ float2 dfn_from(double v)
 {
     const int hiw = __double2hiint(v);
@@ -130,13 +132,10 @@ __device__ __forceinline__ float2 dfn_from(double v)
     const int ex = (hiw >> 20) & 0x7ff;
     const int e = ex - 1023;
     if (ex == 0 || e < -126) return make_float2(0.f, 0.f);
-    if (e < 52 - 126) {
-        const float h = __double2float_rn(v);
-        return make_float2(h, __double2float_rn(v - (double)h));
-    }
     const unsigned sign = (unsigned)hiw & 0x80000000u;
     const unsigned frac23 = (((unsigned)hiw & 0xFFFFFu) << 3) | (low >> 29);
     const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | frac23);
+    if (e < 52 - 126) return make_float2(hi, 0.f);
     // the 29-bit remainder as a float rounded once: two exact 16- and 13-bit halves (2^23 + h - 2^23)
     // and one FMA, no integer-to-float conversion
     const unsigned rem = low & 0x1FFFFFFFu;
