@@ -140,6 +140,15 @@ __device__ __forceinline__ float2 two_sum_rn(float a, float b)
     return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
 
+// a + b for double-float pairs: TwoSum of the high parts, the low parts added, renormalised
+__device__ __forceinline__ float2 df_add2(float2 a, float2 b)
+{
+    const float2 s = two_sum_rn(a.x, b.x);
+    const float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s.x, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s.x)));
+}
+
 // float -> double from the bit pattern (integer pipe; an F2F conversion takes an FP64 issue slot):
 // normal floats exactly, zero and subnormals (far below every value kept here) as 0
 __device__ __forceinline__ double widen_f(float f)
@@ -148,6 +157,17 @@ __device__ __forceinline__ double widen_f(float f)
     const uint32_t ex = (b >> 23) & 0xffu;
     const uint32_t hi = (b & 0x80000000u) | ((ex + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
     return ex ? __hiloint2double((int)hi, (int)(b << 29)) : 0.0;
+}
+
+// the double-float v times 2^e as one double: the scaling in FP32 (exact) where both parts stay
+// within its range, otherwise after widening
+__device__ __forceinline__ double df_out(float2 v, int e)
+{
+    if (e >= -100 && e <= 96) {
+        const float sc = __int_as_float((e + 127) << 23);
+        return widen_f(__fmul_rn(v.x, sc)) + widen_f(__fmul_rn(v.y, sc));
+    }
+    return (widen_f(v.x) + widen_f(v.y)) * pow2i_safe(e);
 }
 
 // tcgen05 shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride between core
@@ -288,7 +308,9 @@ __global__ void tc_scale_kernel(TcArgs A)
 
 // digits of c_lm a_lm for one (m, chunk) in the tile layout of the MMA B operand:
 // [parity][stack][N2 x 16] bf16 with digit s in stack s / 2 at columns n + N (s & 1), core matrix
-// (n2/8, k/8) at ((k/8) (N2/8) + n2/8) * 64 elements; digit 7 is zero
+// (n2/8, k/8) at ((k/8) (N2/8) + n2/8) * 64 elements; digit 7 is zero.  Thread (parity, k/8, n)
+// cuts the 8 values k/8 .. k/8 + 7 of its column: each digit's 8 bf16 are one core-matrix row,
+// 16 contiguous bytes, stored as one vector.
 template <int N>
 __global__ void tc_split_b_kernel(TcArgs A)
 {
@@ -297,26 +319,38 @@ __global__ void tc_split_b_kernel(TcArgs A)
     const int c = (int)(chunk - A.chunk_base[m]);
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
-    __nv_bfloat16 *out = (__nv_bfloat16 *)(A.bdig + chunk * (TcTile<N>::B_CHUNK / 16));
-    for (int t = threadIdx.x; t < 2 * 16 * N; t += blockDim.x) {
-        const int n = t % N, k = (t / N) % 16, eo = t / (16 * N);
-        const int l = m + TC_CH * c + 2 * k + eo;
+    constexpr int N2 = TcTile<N>::N2;
+    uint4 *out = A.bdig + chunk * (TcTile<N>::B_CHUNK / 16);
+    for (int t = threadIdx.x; t < 2 * 2 * N; t += blockDim.x) {
+        const int n = t % N, kh = (t / N) & 1, eo = t / (2 * N);
         const int g = n >> 1;
-        double v = 0.0;
-        if (l <= L && g < A.nmaps) {
-            const int64_t ix = base + (l - m);
-            const double2 a = A.alm[(int64_t)g * A.nalm + ix];
-            const double comp = (n & 1) ? (m == 0 ? 0.0 : a.y) : a.x;
-            v = A.cfac[ix] * comp;
+        const int E = A.Ea[m * N + n];
+        uint32_t pk[TC_S][4];  // per digit, 8 bf16 as 4 pairs
+#pragma unroll
+        for (int kk = 0; kk < 8; kk += 2) {
+            float d0[TC_S], d1[TC_S];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int l = m + TC_CH * c + 2 * (8 * kh + kk + h) + eo;
+                double v = 0.0;
+                if (l <= L && g < A.nmaps) {
+                    const int64_t ix = base + (l - m);
+                    const double2 a = A.alm[(int64_t)g * A.nalm + ix];
+                    const double comp = (n & 1) ? (m == 0 ? 0.0 : a.y) : a.x;
+                    v = A.cfac[ix] * comp;
+                }
+                split_digits(v, E, h ? d1 : d0);
+            }
+            // the digit floats are bf16-exact: a bf16 pair is the upper halves of two floats
+#pragma unroll
+            for (int s = 0; s < TC_S; ++s) pk[s][kk >> 1] = __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
         }
-        float d[TC_S];
-        split_digits(v, A.Ea[m * N + n], d);
-        constexpr int N2 = TcTile<N>::N2;
 #pragma unroll
         for (int s = 0; s < 2 * TcTile<N>::NSTK; ++s) {
             const int n2 = n + N * (s & 1);
-            const int off = ((k >> 3) * (N2 / 8) + (n2 >> 3)) * 64 + (n2 & 7) * 8 + (k & 7);
-            out[(eo * TcTile<N>::NSTK + (s >> 1)) * (N2 * 16) + off] = __float2bfloat16_rn(s < TC_S ? d[s] : 0.f);
+            const int off = (kh * (N2 / 8) + (n2 >> 3)) * 64 + (n2 & 7) * 8;  // elements; a multiple of 8
+            out[((eo * TcTile<N>::NSTK + (s >> 1)) * (N2 * 16) + off) / 8] =
+                s < TC_S ? make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]) : make_uint4(0u, 0u, 0u, 0u);
         }
     }
 }
@@ -745,11 +779,8 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
                     }
                 }
             }
-            double acc[2][NH];
-#pragma unroll
-            for (int eo = 0; eo < 2; ++eo)
-#pragma unroll
-                for (int n = 0; n < NH; ++n) acc[eo][n] = widen_f(fac[eo][n].x) + widen_f(fac[eo][n].y);
+            // Delta_N = E + O, Delta_S = E - O in double-float, scaled by 2^(E_y + E_a - 12) and widened
+            // once per value: 1 FP64 instruction per value instead of a DMUL and a DADD
             if (active) {
                 const int rn = A.slotN[slot], rs = A.slotS[slot];
                 const int64_t mstride = A.mmax + 1;
@@ -757,15 +788,17 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
                 for (int gg = 0; gg < NH / 2; ++gg) {
                     const int g = par * (NH / 2) + gg;  // map
                     if (g < A.nmaps) {
-                        const double sr = pow2i_safe(Ey + A.Ea[m * N + 2 * g] - 12);
-                        const double si = pow2i_safe(Ey + A.Ea[m * N + 2 * g + 1] - 12);
-                        const double er = acc[0][2 * gg] * sr, ei = acc[0][2 * gg + 1] * si;
-                        const double orr = acc[1][2 * gg] * sr, oi = acc[1][2 * gg + 1] * si;
+                        const int er = Ey + A.Ea[m * N + 2 * g] - 12, ei = Ey + A.Ea[m * N + 2 * g + 1] - 12;
+                        const float2 Er = fac[0][2 * gg], Ei = fac[0][2 * gg + 1];
+                        const float2 Or = fac[1][2 * gg], Oi = fac[1][2 * gg + 1];
                         double2 *d = A.delta + (int64_t)g * A.nrings * mstride;
                         if (rn >= 0 && SHT_CHK(rn < A.nrings && m <= A.mmax))
-                            d[(int64_t)rn * mstride + m] = make_double2(er + orr, ei + oi);
+                            d[(int64_t)rn * mstride + m] =
+                                make_double2(df_out(df_add2(Er, Or), er), df_out(df_add2(Ei, Oi), ei));
                         if (rs >= 0 && SHT_CHK(rs < A.nrings && m <= A.mmax))
-                            d[(int64_t)rs * mstride + m] = make_double2(er - orr, ei - oi);
+                            d[(int64_t)rs * mstride + m] = make_double2(
+                                df_out(df_add2(Er, make_float2(-Or.x, -Or.y)), er),
+                                df_out(df_add2(Ei, make_float2(-Oi.x, -Oi.y)), ei));
                     }
                 }
             }
@@ -1155,7 +1188,7 @@ cudaError_t launch_group(const Plan &p, TcArgs A, cudaStream_t st)
 {
     const int64_t nchunks = p.tc_total_chunks;
     tc_scale_kernel<N><<<p.mmax + 1, 256, 0, st>>>(A);
-    tc_split_b_kernel<N><<<(unsigned)nchunks, 256, 0, st>>>(A);
+    tc_split_b_kernel<N><<<(unsigned)nchunks, 4 * N, 0, st>>>(A);  // one thread per (parity, k half, column)
     // one CTA per SM: its shared memory (two stages of tiles and y values) is over half the SM's,
     // and its accumulators take more than half of the tensor memory
     static_assert(TcWs<N>::SMEM > 114 * 1024 && TcWs<N>::SMEM <= 227 * 1024, "one CTA per SM");

@@ -92,6 +92,9 @@ struct F64 {
         return q == 0 ? a : q == 1 ? make_double2(-a.y, a.x) : q == 2 ? make_double2(-a.x, -a.y) : make_double2(a.y, -a.x);
     }
     static __device__ __forceinline__ C half(C a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+    using S = double;  // a real scalar
+    static __device__ __forceinline__ S sfrom(double w) { return w; }
+    static __device__ __forceinline__ C smul(C a, S w) { return make_double2(a.x * w, a.y * w); }
     static __device__ __forceinline__ C from(double2 v) { return v; }
     static __device__ __forceinline__ C from_re_im(double re, double im) { return make_double2(re, im); }
     static __device__ __forceinline__ double2 to(C v) { return v; }
@@ -186,6 +189,9 @@ struct DF {
                         : make_float4(a.z, a.w, -a.x, -a.y);
     }
     static __device__ __forceinline__ C half(C a) { return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w); }
+    using S = float2;  // a real scalar, double-float
+    static __device__ __forceinline__ S sfrom(double w) { return dfn_from(w); }
+    static __device__ __forceinline__ C smul(C a, S w) { return mk(dfn_mul(R(a), w), dfn_mul(I(a), w)); }
     static __device__ __forceinline__ C from(double2 v) { return mk(dfn_from(v.x), dfn_from(v.y)); }
     static __device__ __forceinline__ C from_re_im(double re, double im) { return mk(dfn_from(re), dfn_from(im)); }
     static __device__ __forceinline__ double2 to(C v) { return make_double2(dfn_to(R(v)), dfn_to(I(v))); }
@@ -636,19 +642,19 @@ __device__ void ring_anal_unit(const RingArgs<P> &A, int item, int g, typename P
     }
     const typename P::T *pA = A.phase + (int64_t)it.ringA * mstride;
     double2 *oA = A.delta_out + ((int64_t)g * A.nrings + it.ringA) * mstride;
-    const double wA = A.w[it.ringA];
+    const typename P::S wA = P::sfrom(A.w[it.ringA]);  // the quadrature weight, applied before widening
     const Div by_n(n, A.mmax);
     if (it.ringB < 0) {
         for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
             const int k = m - n * by_n.q(m);
             const C S = P::conj(X[pos ? pos[k] : k]);
-            const double2 v = P::to(P::mulc(P::conjt(pA[m]), S));
-            oA[m] = make_double2(wA * v.x, m == 0 ? 0.0 : wA * v.y);
+            const double2 v = P::to(P::smul(P::mulc(P::conjt(pA[m]), S), wA));
+            oA[m] = make_double2(v.x, m == 0 ? 0.0 : v.y);
         }
     } else {
         const typename P::T *pB = A.phase + (int64_t)it.ringB * mstride;
         double2 *oB = A.delta_out + ((int64_t)g * A.nrings + it.ringB) * mstride;
-        const double wB = A.w[it.ringB];
+        const typename P::S wB = P::sfrom(A.w[it.ringB]);
         for (int m = threadIdx.x; m <= A.mmax; m += blockDim.x) {
             const int k = m - n * by_n.q(m);
             const int kc = k ? n - k : 0;
@@ -657,10 +663,10 @@ __device__ void ring_anal_unit(const RingArgs<P> &A, int item, int g, typename P
             const C SA = P::half(P::add(S, Sc));
             const C D = P::half(P::sub(S, Sc));
             const C SB = P::conj(P::itimes(P::conj(D)));  // D / (2 i) with D halved: -i D
-            const double2 va = P::to(P::mulc(P::conjt(pA[m]), SA));
-            const double2 vb = P::to(P::mulc(P::conjt(pB[m]), SB));
-            oA[m] = make_double2(wA * va.x, m == 0 ? 0.0 : wA * va.y);
-            oB[m] = make_double2(wB * vb.x, m == 0 ? 0.0 : wB * vb.y);
+            const double2 va = P::to(P::smul(P::mulc(P::conjt(pA[m]), SA), wA));
+            const double2 vb = P::to(P::smul(P::mulc(P::conjt(pB[m]), SB), wB));
+            oA[m] = make_double2(va.x, m == 0 ? 0.0 : va.y);
+            oB[m] = make_double2(vb.x, m == 0 ? 0.0 : vb.y);
         }
     }
     __syncthreads();
