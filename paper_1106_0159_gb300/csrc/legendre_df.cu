@@ -58,10 +58,14 @@ __device__ __forceinline__ float2 d2df(double v)
     const unsigned frac23 = (((unsigned)hiw & 0xFFFFFu) << 3) | (low >> 29);
     const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | frac23);
     // lo: the remaining 29 fraction bits times 2^(e - 52), rounded to 24 bits (zero when
-    // 2^(e - 52) is below the normal float range; hi alone then carries 24 bits)
+    // 2^(e - 52) is below the normal float range; hi alone then carries 24 bits).  The 29-bit
+    // integer becomes a float without a conversion instruction (those take an FP64 issue slot on
+    // this part): its 13- and 16-bit halves exactly as (2^23 + h) - 2^23, then one FMA rounds once.
     const unsigned rem = low & 0x1FFFFFFFu;
+    const float rh = __fsub_rn(__uint_as_float(0x4B000000u | (rem >> 16)), 8388608.0f);
+    const float rl = __fsub_rn(__uint_as_float(0x4B000000u | (rem & 0xFFFFu)), 8388608.0f);
     const float sc = (e - 52 >= -126) ? __uint_as_float((unsigned)(e - 52 + 127) << 23) : 0.f;
-    const float lo = (float)rem * sc;
+    const float lo = __fmul_rn(__fmaf_rn(rh, 65536.0f, rl), sc);
     return make_float2(hi, sign ? -lo : lo);
 }
 
@@ -136,7 +140,16 @@ struct DfArgs {
     int64_t part_blk_stride;  // nmaps_total * nalm
 };
 
-__device__ __forceinline__ double widen_df(float2 a) { return (double)a.x + (double)a.y; }
+// float -> double from the bit pattern (integer pipe): normal floats exactly, zero and subnormals as 0
+__device__ __forceinline__ double widen_f1(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned hi = (b & 0x80000000u) | ((ex + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return ex ? __hiloint2double((int)hi, (int)(b << 29)) : 0.0;
+}
+// hi + lo as one double: one DADD, no conversion instructions
+__device__ __forceinline__ double widen_df(float2 a) { return widen_f1(a.x) + widen_f1(a.y); }
 
 template <int N, bool REIN>
 struct DfSmem {

@@ -1099,9 +1099,10 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                     float d[TC_S];
                     split_digits(xv[s][gg][c], e ? e - 1022 : -1000, d);
                     const int off = (r >> 3) * TA_XKB + (row >> 3) * 128 + (row & 7) * 16 + (r & 7) * 2;
+                    // each digit float is bf16-exact: its upper half is the bf16 (no conversion instruction)
 #pragma unroll
                     for (int q = 0; q < TC_S; ++q)
-                        *(__nv_bfloat16 *)(sX + off + q * (TA_R / 8) * 128) = __float2bfloat16_rn(d[q]);
+                        *(unsigned short *)(sX + off + q * (TA_R / 8) * 128) = (unsigned short)(__float_as_uint(d[q]) >> 16);
                 }
 
         const int w8 = warp - 4;  // 0..7
