@@ -891,9 +891,10 @@ __device__ __forceinline__ float2 df_sum(float2 a, float2 b)
 }
 
 // Columns 16 es .. 16 es + 15 (this row's parity) of both y-digit halves of the 4 accumulator
-// regions of chunk buffer tb, this warp's lanes, summed as double-float pairs in the order
-// (region 0 half 0, region 0 half 1, region 1 half 0, ...), classes roughly in decreasing size; the
-// loads go out four at a time and are waited for together.
+// regions of chunk buffer tb, this warp's lanes: regions 0 and 1 summed as double-float pairs in
+// the order (region 0 half 0, region 0 half 1, region 1 half 0, ...), classes roughly in decreasing
+// size, regions 2 and 3 summed in FP32 and added once; the loads go out four at a time and are
+// waited for together.
 __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb, int es, float2 acc[16])
 {
 #pragma unroll
@@ -915,13 +916,25 @@ __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb,
                 : "r"(addr));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (h0 == 0) {  // regions t = 0, 2 (classes 0-4): double-float
 #pragma unroll
-        for (int hh = 0; hh < 4; ++hh)
+            for (int hh = 0; hh < 4; ++hh)
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float2 sm = two_sum(acc[t].x, __uint_as_float(v[hh][t]));
+                    acc[t] = make_float2(sm.x, acc[t].y + sm.y);
+                }
+        } else {
+            // regions t = 4, 6 (classes 4-8, at most about 2^-28 of the sum): added in FP32 (an error
+            // near 2^-52 of the sum), then into the pair once
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-                const float2 sm = two_sum(acc[t].x, __uint_as_float(v[hh][t]));
+                const float small = (__uint_as_float(v[0][t]) + __uint_as_float(v[1][t])) +
+                                    (__uint_as_float(v[2][t]) + __uint_as_float(v[3][t]));
+                const float2 sm = two_sum(acc[t].x, small);
                 acc[t] = make_float2(sm.x, acc[t].y + sm.y);
             }
+        }
     }
 }
 
