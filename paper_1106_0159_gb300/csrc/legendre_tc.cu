@@ -849,16 +849,17 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
 
 constexpr int TA_R = 64;                          // rows: [Sigma | D] x 16 maps x (re, im)
 constexpr int TA_MAPS = 16;                       // maps per launch
-constexpr int TA_XD = TC_S + 1;                   // digits of X and of y in shared memory (the last one zero)
+constexpr int TA_XD = TC_S + 1;                   // digits of y in shared memory (the last one zero)
+constexpr int TA_XDX = TC_S;                      // digits of X in shared memory (no zero digit: see below)
 constexpr int TA_REG = 4;                         // accumulator regions per chunk (t = 0, 2, 4, 6)
 constexpr int TA_N = 2 * TC_CH;                   // MMA N: two y digits of one 32-l chunk
 constexpr int TA_YS = TC_T + 4;                   // y stage row stride (doubles): conflict-free pair loads
-constexpr int TA_XBYTES = TA_XD * TA_R * TC_T * 2;  // X digits, [slot / 8][digit][row / 8] core matrices
-constexpr int TA_XKB = TA_XD * (TA_R / 8) * 128;  // bytes between 8-slot groups of the X operand
+constexpr int TA_XBYTES = TA_XDX * TA_R * TC_T * 2;  // X digits, [slot / 8][digit][row / 8] core matrices
+constexpr int TA_XKB = TA_XDX * (TA_R / 8) * 128; // bytes between 8-slot groups of the X operand
 constexpr int TA_BDIG = (TC_CH / 8) * 128;        // one digit of one 8-slot group of a K-step's y tile
 constexpr int TA_BKB = TA_XD * TA_BDIG;           // bytes between the two 8-slot groups of a y tile
 constexpr int TA_BTILE = 2 * TA_BKB;              // one K-step's y tile, [slot / 8][digit][l / 8] core matrices
-constexpr int TA_NB = 3;                          // y tile buffers (K-steps in flight between split and MMA)
+constexpr int TA_NB = 5;                          // y tile buffers (K-steps in flight between split and MMA)
 constexpr int TA_ACC = TA_REG * TA_N;             // tensor-memory columns of one chunk's accumulators
 constexpr int TA_OFF_B = TA_XBYTES;
 constexpr int TA_OFF_Y = TA_OFF_B + TA_NB * TA_BTILE;
@@ -874,6 +875,7 @@ enum : int { BAR_EPI = 7, BAR_PREP = 8 };         // epilogue warps; split + epi
 static_assert(2 * TA_ACC <= TA_TMEM_COLS, "two accumulator sets fit the allocation");
 static_assert(TA_SMEM > 114 * 1024 && TA_SMEM <= 227 * 1024, "one CTA per SM (it holds all tensor memory)");
 static_assert(TC_S == 7 && TA_XD == 8, "the digit stacks pair digits 0-1, 2-3, 4-5, 6-7");
+static_assert(TA_OFF_B + 1024 <= TA_SMEM, "the last X group's stack [X_6 ; next] stays in shared memory");
 static_assert(TC_MAXW == 6, "regions t = 0, 2, 4, 6 cover the products of classes up to 6");
 
 __device__ __forceinline__ float2 two_sum(float a, float b)
@@ -926,11 +928,14 @@ __device__ __forceinline__ void read_regions(uint32_t tmem, int quarter, int tb,
                 }
         } else {
             // regions t = 4, 6 (classes 4-8, at most about 2^-28 of the sum): added in FP32 (an error
-            // near 2^-52 of the sum), then into the pair once
+            // near 2^-52 of the sum), then into the pair once.  The bottom half of region 6 (lane
+            // quarters 2, 3: classes 7 and 8 only) is left out: X has no zero digit 7 in shared memory
+            // (the a = 6 stack reads other digits there), and those classes lie near 2^-49 of the sum.
+            const bool bottom = quarter >= 2;
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 const float small = (__uint_as_float(v[0][t]) + __uint_as_float(v[1][t])) +
-                                    (__uint_as_float(v[2][t]) + __uint_as_float(v[3][t]));
+                                    (bottom ? 0.f : __uint_as_float(v[2][t]) + __uint_as_float(v[3][t]));
                 const float2 sm = two_sum(acc[t].x, small);
                 acc[t] = make_float2(sm.x, acc[t].y + sm.y);
             }
@@ -1089,13 +1094,12 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
                     const unsigned e = __reduce_max_sync(0xffffffffu, (unsigned)dexp(xv[s][gg][c]));
                     if (lane == 0 && e) atomicMax(&sEx[32 * s + 2 * (8 * hh + gg) + c], (int)e);
                 }
-        // the zero digits X_7 and Y_7 (the second halves of the last stacks)
-        for (int t = sp; t < TA_XBYTES / 16 / TA_XD; t += 2 * TC_T) {
-            const int kb = t / (TA_R / 8 * 8), rest = t - kb * (TA_R / 8 * 8);
-            *(uint4 *)(sX + kb * TA_XKB + (TC_S * (TA_R / 8)) * 128 + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        if (sp < TA_NB * 2 * TA_BDIG / 16) {  // [buffer][8-slot group]
-            const int g2 = sp / (TA_BDIG / 16), rest = sp - g2 * (TA_BDIG / 16);
+        // the zero digit Y_7 (the second half of the last stack of every y tile); X has no digit 7:
+        // the stack [X_6 ; X_7] of the a = 6 MMA reads the next 8-slot group's first digit there,
+        // whose products land only in the bottom half of region t = 6 (classes 7 and 8), which the
+        // epilogue leaves out
+        for (int t = sp; t < TA_NB * 2 * TA_BDIG / 16; t += 2 * TC_T) {  // [buffer][8-slot group]
+            const int g2 = t / (TA_BDIG / 16), rest = t - g2 * (TA_BDIG / 16);
             *(uint4 *)(sY + g2 * TA_BKB + TC_S * TA_BDIG + rest * 16) = make_uint4(0u, 0u, 0u, 0u);
         }
         bar_sync(BAR_PREP, 2 * TC_T + TA_NEPI);  // row exponents complete (the epilogue reads them too)
