@@ -87,10 +87,10 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings,
  *                        FP64 or double-float.  The ring DFTs run in double-float on the FP32 pipe.
  *                        SHT_TUNE_PREC_ANAL and SHT_TUNE_PREC_RING select other kernels.  Relative
  *                        error against the exact transform <= 1e-9 of the output RMS.  Processes up
- *                        to 16 maps per pass over the recurrence.  Only the first 128 ring slots
+ *                        to 16 maps per pass over the recurrence.  Only the first 256 ring slots
  *                        (after north/south pairing, ordered from the poles) may lie within
  *                        sin(theta) < 0.03 of a pole; a grid with more polar slots (HEALPix
- *                        Nside >~ 3500) returns SHT_EUNSUPPORTED and stays in its old mode.
+ *                        Nside >~ 7000) returns SHT_EUNSUPPORTED and stays in its old mode.
  * Switching to SHT_MODE_SPLIT_BF16 the first time runs one FP64 pass of the recurrence to
  * measure the scale of its values per (m, block of 128 ring slots) (synchronous; about the cost
  * of one single-map synthesis).  SHT_EINVAL for an unknown mode.

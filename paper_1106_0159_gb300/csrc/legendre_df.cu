@@ -369,16 +369,17 @@ __global__ void __launch_bounds__(DFS_T) synth_df_polar_kernel(DfSynArgs A)
     __shared__ float4 sa[NM][DF_CHL];    // a_lm of the chunk as (re_hi, re_lo, im_hi, im_lo)
     const int m = blockIdx.x;
     const int tid = threadIdx.x;
-    const bool active = tid < A.nslots;
+    const int slot = (int)blockIdx.y * DFS_T + tid;  // block y of the polar slot blocks
+    const bool active = slot < A.nslots;
     const int L = A.lmax;
     const int64_t base = (int64_t)m * (2 * L + 3 - m) / 2;
 
     double u = 0.0, y1 = 0.0, y2 = 0.0;  // y1: lambda_(l-1), y2: D_(l-1)
     int k = 0;
     if (active) {
-        u = A.u[tid];
+        u = A.u[slot];
         double y0;
-        sectoral_start(A.s[tid], A.alpha[base], m, y0, k);
+        sectoral_start(A.s[slot], A.alpha[base], m, y0, k);
         y2 = y0;  // D_(m-1) = lambda_m with lambda_(m-1) = 0
     }
     float2 acc[2][NM][2];  // [E, O][map][re, im]
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(DFS_T) synth_df_polar_kernel(DfSynArgs A)
         }
     }
     if (active) {
-        const int rn = A.slotN[tid], rs = A.slotS[tid];
+        const int rn = A.slotN[slot], rs = A.slotS[slot];
         const int64_t mstride = A.mmax + 1;
 #pragma unroll
         for (int g = 0; g < NM; ++g) {
@@ -523,7 +524,7 @@ cudaError_t launch_legendre_synth_df_polar(const Plan &p, const double2 *alm, do
     A.s = p.d_s;
     A.alpha = p.d_alpha;
     A.rein = p.d_rein;
-    A.nslots = std::min(p.nslots, DFS_T);
+    A.nslots = p.nslots;
     A.lmax = p.lmax;
     A.mmax = p.mmax;
     A.nrings = p.nrings;
@@ -535,9 +536,9 @@ cudaError_t launch_legendre_synth_df_polar(const Plan &p, const double2 *alm, do
         A.alm = alm + (int64_t)g0 * p.nalm;
         A.delta = delta + (int64_t)g0 * dstride;
         if (nm > 4)
-            synth_df_polar_kernel<8><<<(unsigned)(p.mR + 1), DFS_T, 0, st>>>(A);
+            synth_df_polar_kernel<8><<<dim3((unsigned)(p.mR + 1), (unsigned)p.polar_syn_blocks), DFS_T, 0, st>>>(A);
         else
-            synth_df_polar_kernel<4><<<(unsigned)(p.mR + 1), DFS_T, 0, st>>>(A);
+            synth_df_polar_kernel<4><<<dim3((unsigned)(p.mR + 1), (unsigned)p.polar_syn_blocks), DFS_T, 0, st>>>(A);
         ++*nlaunch;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

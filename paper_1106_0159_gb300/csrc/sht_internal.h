@@ -111,6 +111,8 @@ struct Plan {
     double4 *d_spin_tab = nullptr;      // spin 2: [nalm] (alpha, alpha (1 + g), alpha (1 - g), c), built on first use
     double *d_spin_start = nullptr;     // spin 2: [mmax + 1] start coefficients S_m
     bool polar_first_slot = false;      // slot 0 runs the Reinsch form (sin(theta) < 0.03)
+    int polar_syn_blocks = 0;     // leading 128-slot blocks whose first slot is polar (sin < 0.03): the
+                                  // precision-form synthesis runs them in the Reinsch form for m <= mR
 
     // launch tuning (sht_tune): maps or slots per thread per launch
     int tune[SHT_TUNE_COUNT] = {4, 2, 4, 8, 16, 1, 1, 2};

@@ -474,8 +474,9 @@ sht_status sht_plan_set_mode(sht_plan_t plan, int mode)
     if (!plan || (mode != SHT_MODE_FP64 && mode != SHT_MODE_SPLIT_BF16)) return SHT_EINVAL;
     Plan &p = plan->p;
     if (mode == SHT_MODE_SPLIT_BF16) {
-        // only slot block 0 (128 slots) may be polar: its Reinsch CTAs run in FP64
-        if (p.nslots > 128 && p.slotTheta[128] > 0.0 && std::sin(p.slotTheta[128]) < 0.03) return SHT_EUNSUPPORTED;
+        // the Reinsch-form kernels of the precision form cover the first 256 slots (the analysis: one
+        // CTA over slots 0 .. 255 per m; the synthesis: the leading polar 128-slot blocks)
+        if (p.nslots > 256 && p.slotTheta[256] > 0.0 && std::sin(p.slotTheta[256]) < 0.03) return SHT_EUNSUPPORTED;
         cudaError_t e = sht::build_tc_scales(p);  // one FP64 pass of the recurrence, synchronous
         if (e == cudaSuccess) e = sht::build_df_ring_tables(p);
         if (e != cudaSuccess) return cuda_fail(p, e, "precision-form tables");
@@ -613,6 +614,9 @@ sht_status sht_plan_create(sht_plan_t *out, sht_grid grid, int nrings, const int
     std::vector<double3> rein;
     reinsch_tables(lmax, p.mR, rein);
     p.polar_first_slot = p.mR >= 0 && s[0] < 0.03;
+    p.polar_syn_blocks = 0;
+    if (p.mR >= 0)
+        while (p.polar_syn_blocks * 128 < p.nslots && s[p.polar_syn_blocks * 128] < 0.03) ++p.polar_syn_blocks;
     p.tune[SHT_TUNE_ANAL_SLOTS] = sht::legendre_anal_default_slots(p);
     // precision form: 32-l chunks per m
     std::vector<int64_t> chunk_base(mmax + 1);

@@ -217,3 +217,47 @@ def test_full_size_round_trip_on_the_red_input():
     assert worst < 2e-9
     assert p.device_status() == 0
     p.close()
+
+
+def _polar_geometry(npolar, nother=100, nphi=72):
+    # npolar unpaired northern rings within sin(theta) < 0.03 of the pole, then nother rings further
+    # south: the first ceil(npolar / 128) slot blocks start polar
+    rng = np.random.default_rng(44)
+    th = np.concatenate([np.sort(rng.uniform(5e-4, 0.0295, npolar)),
+                         np.sort(rng.uniform(0.06, 1.5, nother))])
+    n = len(th)
+    nphi_a = np.full(n, nphi, np.int64)
+    phi0 = rng.uniform(0, 2 * np.pi, n)
+    w = rng.uniform(0.5, 2.0, n) * 1e-3
+    return nphi_a, th, phi0, w
+
+
+def test_polar_slots_over_two_blocks():
+    """200 polar ring slots: slot blocks 0 and 1 both start within sin(theta) < 0.03 and run in
+    the Reinsch form (synthesis: both blocks; analysis: slots 0 .. 255) for m <= mR; both directions
+    against the plain FP64 path and the synthesis against the oracle on polar rings of both blocks."""
+    from paper_1106_0159_gb300 import sht
+    geom = _polar_geometry(200)
+    L = 96
+    q = _plain(geom, L)
+    p = _plan(geom, L)
+    a = inputs.gaussian_alm(L, L, seed=45, nmaps=3)
+    s_tc, s_64 = host(p.alm2map(dev(a))), host(q.alm2map(dev(a)))
+    for g in range(3):
+        assert rel(s_tc[g], s_64[g]) < TOL_TC, g
+    off = geometry.ring_offsets(geom)
+    rings = [0, 60, 127, 128, 150, 199, 200, 260]
+    ref = oracle.alm2map_rings(geom, a[1], L, L, rings)
+    got = np.concatenate([s_tc[1][off[r]:off[r + 1]] for r in rings])
+    assert rel(got, ref) < TOL_TC
+    m = inputs.white_map(geometry.npix(geom), seed=46, nmaps=3)
+    b_tc, b_64 = host(p.map2alm(dev(m))), host(q.map2alm(dev(m)))
+    for g in range(3):
+        assert rel(b_tc[g], b_64[g]) < TOL_TC, g
+    assert p.device_status() == 0
+    # more than 256 polar slots: refused, the plan stays in FP64
+    r = sht.Plan(_polar_geometry(300), L)
+    with pytest.raises(sht.ShtError) as e:
+        r.set_mode(sht.MODE_SPLIT_BF16)
+    assert e.value.status == sht.SHT_EUNSUPPORTED
+    assert r.mode == sht.MODE_FP64
