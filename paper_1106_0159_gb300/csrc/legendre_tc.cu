@@ -225,7 +225,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
-            : "r"(a), "r"(parity));
+            : "r"(a), "r"(parity)
+            : "memory");  // acquire: no shared-memory access moves above a successful wait
         if (done) return true;
         if (it > 64) __nanosleep(32);
     }
@@ -709,8 +710,6 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
 #pragma unroll
             for (int i = 0; i < BV; ++i)
                 if (i * NS + sp < BTOT) breg[i] = bsrc[i * NS + sp];
-            // the MMAs of chunk q - 2 read this stage's tiles: wait (bounded) before rewriting them
-            if (q >= 2 && ok && !mbar_wait(&mbar[st], (uint32_t)(((q >> 1) - 1) & 1))) ok = false;
             bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
             const double *yb = ybuf + (size_t)st * TC_CH * TC_T;
 #pragma unroll 1
@@ -727,6 +726,9 @@ __global__ void __launch_bounds__(TC_NT + 32, 1) tc_synth_kernel(TcArgs A)
                         pk[s][qq >> 1] = __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
                 }
                 if (h == 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TC_NT);  // y stage read
+                // the MMAs of chunk q - 2 read this stage's tiles: wait (bounded) before rewriting them
+                // (after the first half is cut, which only reads the y stage)
+                if (h == 0 && q >= 2 && ok && !mbar_wait(&mbar[st], (uint32_t)(((q >> 1) - 1) & 1))) ok = false;
                 // k-group h of this parity's A tiles: core matrix (slot/8, h), row slot%8
                 const int off = ((h * 16) + (r >> 3)) * 128 + (r & 7) * 16;
 #pragma unroll
@@ -860,6 +862,8 @@ constexpr int TA_BDIG = (TC_CH / 8) * 128;        // one digit of one 8-slot gro
 constexpr int TA_BKB = TA_XD * TA_BDIG;           // bytes between the two 8-slot groups of a y tile
 constexpr int TA_BTILE = 2 * TA_BKB;              // one K-step's y tile, [slot / 8][digit][l / 8] core matrices
 constexpr int TA_NB = 5;                          // y tile buffers (K-steps in flight between split and MMA)
+constexpr int TA_SK = 2;                          // K-steps a split thread cuts per iteration
+static_assert((TC_T / 16) % TA_SK == 0 && TA_SK < TA_NB, "K-steps per split iteration");
 constexpr int TA_ACC = TA_REG * TA_N;             // tensor-memory columns of one chunk's accumulators
 constexpr int TA_OFF_B = TA_XBYTES;
 constexpr int TA_OFF_Y = TA_OFF_B + TA_NB * TA_BTILE;
@@ -1134,22 +1138,37 @@ __global__ void __launch_bounds__(TA_NT, 1) tc_anal_kernel(TcArgs A)
             bar_sync(BAR_FULL + st, TC_NT);  // y of chunk q is in its stage
             const double *yb = ybuf + (size_t)st * TC_CH * TA_YS;
 #pragma unroll 1
-            for (int kk = 0; kk < TC_T / 16; ++kk) {
-                const int gk = 8 * q + kk, b = gk % TA_NB;
-                unsigned char *yt = sY + b * TA_BTILE;
-                // the MMAs of K-step gk - NB read this buffer: wait (bounded) before rewriting it
-                if (gk >= TA_NB && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk / TA_NB) - 1) & 1))) ok = false;
-                const double2 yy = *reinterpret_cast<const double2 *>(yb + jrow * TA_YS + 16 * kk + 8 * kh + 2 * kp);
-                float d0[TC_S], d1[TC_S];
-                split_digits(yy.x, Ey, d0);
-                split_digits(yy.y, Ey, d1);
-                if (kk == TC_T / 16 - 1 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TC_NT);  // y stage read
+            for (int kk = 0; kk < TC_T / 16; kk += TA_SK) {
+                // TA_SK K-steps at a time: 2 TA_SK independent values per thread (one K-step at a
+                // time left the split warps latency-bound: 181 against 175 ms at lmax 4096, 16 maps)
+                double2 yy[TA_SK];
 #pragma unroll
-                for (int s = 0; s < TC_S; ++s)
-                    *(uint32_t *)(yt + s * TA_BDIG + boff) =
-                        __byte_perm(__float_as_uint(d0[s]), __float_as_uint(d1[s]), 0x7632);
-                asm volatile("fence.proxy.async.shared::cta;");
-                asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
+                for (int u = 0; u < TA_SK; ++u)
+                    yy[u] = *reinterpret_cast<const double2 *>(yb + jrow * TA_YS + 16 * (kk + u) + 8 * kh + 2 * kp);
+#pragma unroll
+                for (int u = 0; u < TA_SK; ++u) {
+                    const int gk = 8 * q + kk + u, b = gk % TA_NB;
+                    // the MMAs of K-step gk - NB read buffer b: wait (bounded) before rewriting it
+                    if (gk >= TA_NB && ok && !mbar_wait(&mbar[b], (uint32_t)(((gk / TA_NB) - 1) & 1))) ok = false;
+                }
+                float d0[TA_SK][TC_S], d1[TA_SK][TC_S];
+#pragma unroll
+                for (int u = 0; u < TA_SK; ++u) {
+                    split_digits(yy[u].x, Ey, d0[u]);
+                    split_digits(yy[u].y, Ey, d1[u]);
+                }
+                if (kk + TA_SK == TC_T / 16 && q + 2 < nlive) bar_arrive(BAR_EMPTY + st, TC_NT);  // y stage read
+#pragma unroll
+                for (int u = 0; u < TA_SK; ++u) {
+                    const int b = (8 * q + kk + u) % TA_NB;
+                    unsigned char *yt = sY + b * TA_BTILE;
+#pragma unroll
+                    for (int s = 0; s < TC_S; ++s)
+                        *(uint32_t *)(yt + s * TA_BDIG + boff) =
+                            __byte_perm(__float_as_uint(d0[u][s]), __float_as_uint(d1[u][s]), 0x7632);
+                    asm volatile("fence.proxy.async.shared::cta;");
+                    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
+                }
             }
         }
         if (!ok && lane == 0) atomicOr(A.status, 1);

@@ -36,6 +36,10 @@ namespace {
 #define RING_CTAS_PER_SM 2
 #endif
 constexpr int FFT_T = RING_T;
+// Threads of the double-float DFT kernels that run one CTA per SM (shared-memory DFTs too large
+// for two): 1024 at 64 registers each (lmax 4096, HEALPix 2048, 16 maps: synthesis / analysis
+// 42.4 / 38.0 ms, against 46.4 / 38.8 with 512 threads at 128 registers); the FP64 ones keep 512.
+constexpr int RING_DF_WIDE_T = 1024;
 
 #include "check.cuh"
 constexpr int MAXR = 13;
@@ -122,6 +126,24 @@ __device__ __forceinline__ float2 dfn_mul(float2 a, float2 b)
     const float h = p + e;
     return make_float2(h, e - (h - p));
 }
+// a b + sg c d (sg = +-1) as one double-float: the two leading products exact by FMA, their sum by
+// TwoSum, the four cross terms of the low parts added into the error term, one renormalisation
+// (19 FP32 operations against 23 for two products and a sum)
+__device__ __forceinline__ float2 dfn_dot2(float2 a, float2 b, float2 c, float2 d, float sg)
+{
+    const float p1 = a.x * b.x, p2 = sg * (c.x * d.x);
+    const float e1 = fmaf(a.x, b.x, -p1), e2 = fmaf(sg * c.x, d.x, -p2);
+    const float s = p1 + p2;
+    const float v = s - p1;
+    float t = (p1 - (s - v)) + (p2 - v);
+    t += e1 + e2;
+    t = fmaf(a.x, b.y, t);
+    t = fmaf(a.y, b.x, t);
+    t = fmaf(sg * c.x, d.y, t);
+    t = fmaf(sg * c.y, d.x, t);
+    const float h = s + t;
+    return make_float2(h, t - (h - s));
+}
 // FP64 -> (hi, lo) from the bit pattern, on the integer pipe (an FP64 <-> FP32 conversion takes an
 // FP64 issue slot, 1/64 of the FP32 rate on this part): hi = sign, exponent and the top 23 fraction
 // bits; lo = the remaining 29 bits, rounded to 24.  Below 2^-74 the remainder would leave the FP32
@@ -173,9 +195,7 @@ struct DF {
     }
     static __device__ __forceinline__ C mulc(C a, C b)
     {
-        const float2 re = dfn_add(dfn_mul(R(a), R(b)), dfn_neg(dfn_mul(I(a), I(b))));
-        const float2 im = dfn_add(dfn_mul(R(a), I(b)), dfn_mul(I(a), R(b)));
-        return mk(re, im);
+        return mk(dfn_dot2(R(a), R(b), I(a), I(b), -1.f), dfn_dot2(R(a), I(b), I(a), R(b), 1.f));
     }
     static __device__ __forceinline__ C mul(C a, T b) { return mulc(a, b); }
     static __device__ __forceinline__ C conj(C a) { return make_float4(a.x, a.y, -a.z, -a.w); }
@@ -597,8 +617,8 @@ __device__ void ring_synth_unit(const RingArgs<P> &A, int item, int g, typename 
 }
 
 // MINB: CTAs per SM the register budget is set for (1 where the shared memory allows only one)
-template <class P, int MINB>
-__global__ void __launch_bounds__(FFT_T, MINB) ring_synth_kernel(RingArgs<P> A)
+template <class P, int MINB, int NT = FFT_T>
+__global__ void __launch_bounds__(NT, MINB) ring_synth_kernel(RingArgs<P> A)
 {
     using C = typename P::C;
     C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
@@ -672,8 +692,8 @@ __device__ void ring_anal_unit(const RingArgs<P> &A, int item, int g, typename P
     __syncthreads();
 }
 
-template <class P, int MINB>
-__global__ void __launch_bounds__(FFT_T, MINB) ring_anal_kernel(RingArgs<P> A)
+template <class P, int MINB, int NT = FFT_T>
+__global__ void __launch_bounds__(NT, MINB) ring_anal_kernel(RingArgs<P> A)
 {
     using C = typename P::C;
     C *B0 = A.scratch + (int64_t)blockIdx.x * 3 * A.maxlen;
@@ -849,9 +869,9 @@ cudaError_t ring_kernel_attributes()
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
         cudaError_t e = cudaSuccess;
         const void *k[] = {(const void *)ring_synth_kernel<F64, 1>,      (const void *)ring_synth_kernel<F64, 2>,
-                           (const void *)ring_synth_kernel<DF, 1>,       (const void *)ring_synth_kernel<DF, 2>,
+                           (const void *)ring_synth_kernel<DF, 1, RING_DF_WIDE_T>, (const void *)ring_synth_kernel<DF, 2>,
                            (const void *)ring_anal_kernel<F64, 1>,       (const void *)ring_anal_kernel<F64, 2>,
-                           (const void *)ring_anal_kernel<DF, 1>,        (const void *)ring_anal_kernel<DF, 2>,
+                           (const void *)ring_anal_kernel<DF, 1, RING_DF_WIDE_T>, (const void *)ring_anal_kernel<DF, 2>,
                            (const void *)ring_batch_kernel<F64, true, 1>, (const void *)ring_batch_kernel<F64, true, 2>,
                            (const void *)ring_batch_kernel<F64, false, 1>,
                            (const void *)ring_batch_kernel<F64, false, 2>};
@@ -952,7 +972,8 @@ bool ring_sm(const Plan &p)
 // dynamic shared memory of one ring launch
 int ring_smem_bytes(const Plan &p) { return ring_sm(p) ? p.ring_smem : 0; }
 
-// one CTA per SM: the kernels built for 128 registers per thread
+// one CTA per SM: the kernels built for one resident CTA (FP64: 512 threads at 128 registers,
+// double-float: RING_DF_WIDE_T threads)
 bool ring_wide(const Plan &p) { return ring_sm(p) && p.ring_occ < 2; }
 
 }  // namespace
@@ -1007,7 +1028,7 @@ cudaError_t launch_ring_synth_grid(const Plan &p, const double2 *delta, double *
         A.delta_in = delta;
         A.map_out = map;
         if (ring_wide(p))
-            ring_synth_kernel<DF, 1><<<grid, FFT_T, ring_smem_bytes(p), st>>>(A);
+            ring_synth_kernel<DF, 1, RING_DF_WIDE_T><<<grid, RING_DF_WIDE_T, ring_smem_bytes(p), st>>>(A);
         else
             ring_synth_kernel<DF, 2><<<grid, FFT_T, ring_smem_bytes(p), st>>>(A);
     } else {
@@ -1036,7 +1057,7 @@ cudaError_t launch_ring_anal(const Plan &p, const double *map, double2 *delta, d
         A.map_in = map;
         A.delta_out = delta;
         if (ring_wide(p))
-            ring_anal_kernel<DF, 1><<<ring_grid(p), FFT_T, ring_smem_bytes(p), st>>>(A);
+            ring_anal_kernel<DF, 1, RING_DF_WIDE_T><<<ring_grid(p), RING_DF_WIDE_T, ring_smem_bytes(p), st>>>(A);
         else
             ring_anal_kernel<DF, 2><<<ring_grid(p), FFT_T, ring_smem_bytes(p), st>>>(A);
     } else {
