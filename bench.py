@@ -430,6 +430,37 @@ def ours_arm(a, rank, world, local_rank):
                 "algorithmic_bytes": alg,
                 "traffic_over_algorithmic": (traffic / alg) if traffic else None}
 
+    # ring stages (eqs. Delta2map and almfftdef): one launch per call and direction.  Algorithmic
+    # bytes per call = Delta (written or read) + maps (read or written) + the phase table once;
+    # nominal FFT work = 2.5 n log2 n flops per real ring of n pixels (one complex DFT carries two)
+    nphi_r = np.asarray(geom[0], dtype=np.float64)
+    fft_flops_map = float(2.5 * np.sum(nphi_r * np.log2(nphi_r)))
+    hbm_peak = MEASURED.get("hbm_gbs") or 6800.0
+
+    def ring_stages(run, steps, double_float):
+        out = {}
+        for key in ("ring_synth", "ring_anal"):
+            ms, n = run["stages"].get(key, (0.0, 0))
+            if not n:
+                continue
+            per_call_s = ms * 1e-3 / steps
+            alg = B * (plan.nrings * (L + 1) * 16 + npix * 8) + plan.nrings * (L + 1) * 16
+            gbs = alg / per_call_s / 1e9
+            tf = B * fft_flops_map / per_call_s / 1e12
+            r = {"ms_per_call": per_call_s * 1e3, "algorithmic_bytes": alg, "achieved_gbs": gbs,
+                 "hbm_peak_gbs": hbm_peak, "hbm_frac": gbs / hbm_peak,
+                 "fft_tflops_nominal": tf, "fp64_peak_tflops": peak_tf, "fp64_frac": tf / peak_tf}
+            if double_float:
+                # profiles/traffic.json records the double-float global-scratch DFTs at 16 maps per call
+                tr = traffic_from_profiles(key + "_kernel") if B == 16 else None
+                r["traffic"] = tr
+                r["traffic_over_algorithmic"] = (tr / alg) if tr else None
+            out[key] = r
+        out["note"] = ("nominal FFT flops (no Bluestein overhead) over the stage's CUDA-event time; %s" %
+                       ("double-float arithmetic on the FP32 pipe: fp64_frac is the FP64-equivalent rate"
+                        if double_float else "FP64 arithmetic"))
+        return out
+
     head = timed(a.mode, a.steps, a.warmup, True)
     total_ms, step_ms, stages, clk = head["total_ms"], head["step_ms"], head["stages"], head["clocks"]
     value = job_throughput(world, B * a.steps, total_ms)
@@ -442,7 +473,8 @@ def ours_arm(a, rank, world, local_rank):
         plain = {"value": job_throughput(world, B * a.plain_steps, pr["total_ms"]), "unit": "maps/s",
                  "ms_per_step": pr["total_ms"] / a.plain_steps, "steps": a.plain_steps, "warmup": 1,
                  "stages_ms_per_step": {k: v[0] / a.plain_steps for k, v in pr["stages"].items()},
-                 "roofline": fp64_roofline(pr, a.plain_steps)}
+                 "roofline": fp64_roofline(pr, a.plain_steps),
+                 "ring_stages": ring_stages(pr, a.plain_steps, False)}
         plan.set_mode(sht.MODE_SPLIT_BF16)
 
     # end to end: pinned host a_lm -> device, round trip, result back to pinned host memory, every
@@ -576,6 +608,7 @@ def ours_arm(a, rank, world, local_rank):
                            "per": "step (%d-map round trip)" % B},
             "roofline": roofline,
             "stages_ms_per_step": {k: v[0] / a.steps for k, v in stages.items()},
+            "ring_stages": ring_stages(head, a.steps, a.mode == "split" and plan.tuning(sht.TUNE_PREC_RING) == 1),
             "plain": plain,
             "accuracy": accuracy,
             "serve": None,
