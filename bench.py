@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--mode", default="split", choices=["split", "fp64"],
                     help="split: precision form, tensor-core synthesis and analysis (<= 1e-9); fp64: plain")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 comparison")
-    ap.add_argument("--serve-requests", type=int, default=120, help="requests in the serving trace (0: no serving leg)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests in the serving trace (0: no serving leg)")
     ap.add_argument("--batch-maps", type=int, default=256, help="maps in the batched-form leg (0: no batched leg)")
     ap.add_argument("--no-c2", dest="c2", action="store_false",
                     help="skip the plain FP64 lmax = 2048 leg (HEALPix 1024 and the Gauss-Legendre round trip)")
@@ -287,6 +287,43 @@ def traffic_from_profiles(kernel_key):
     return rec.get("bytes_per_launch")
 
 
+def ring_stage_figures(stages, steps, nmaps, nrings, mmax, npix, nphi, hbm_peak_gbs, fp64_peak_tflops,
+                       double_float=False, traffic_lookup=None):
+    """Ring stages (eqs. Delta2map and almfftdef), one launch per call and direction, from the
+    per-stage CUDA-event times {name: (ms over `steps` calls, launches)}.  Algorithmic bytes per
+    call: Delta (nmaps x nrings x (mmax + 1) complex128, written or read) + maps (nmaps x npix
+    float64, read or written) + the phase table once (nrings x (mmax + 1) x 16 B).  Nominal FFT
+    work: 2.5 n log2 n flops per real ring of n pixels and map (a complex DFT of length n carries
+    two rings at 5 n log2 n); Bluestein's extra work is not counted.  `double_float`: the DFTs ran in
+    double-float arithmetic (FP32 pipe); `traffic_lookup(kernel)` gives the recorded DRAM bytes of a
+    launch (the double-float DFTs at 16 maps), or None."""
+    import numpy as np
+
+    nphi = np.asarray(nphi, dtype=np.float64)
+    fft_flops_map = float(2.5 * np.sum(nphi * np.log2(nphi)))
+    alg = nmaps * (nrings * (mmax + 1) * 16 + npix * 8) + nrings * (mmax + 1) * 16
+    out = {}
+    for key in ("ring_synth", "ring_anal"):
+        ms, n = stages.get(key, (0.0, 0))
+        if not n:
+            continue
+        per_call_s = ms * 1e-3 / steps
+        gbs = alg / per_call_s / 1e9
+        tf = nmaps * fft_flops_map / per_call_s / 1e12
+        r = {"ms_per_call": per_call_s * 1e3, "algorithmic_bytes": alg, "achieved_gbs": gbs,
+             "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": gbs / hbm_peak_gbs, "fft_tflops_nominal": tf,
+             "fp64_peak_tflops": fp64_peak_tflops, "fp64_frac": tf / fp64_peak_tflops}
+        if traffic_lookup is not None:
+            tr = traffic_lookup(key + "_kernel")
+            r["traffic"] = tr
+            r["traffic_over_algorithmic"] = (tr / alg) if tr else None
+        out[key] = r
+    out["note"] = ("nominal FFT flops (no Bluestein overhead) over the stage's CUDA-event time; %s" %
+                   ("double-float arithmetic on the FP32 pipe: fp64_frac is the FP64-equivalent rate"
+                    if double_float else "FP64 arithmetic"))
+    return out
+
+
 def ours_arm(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -430,36 +467,11 @@ def ours_arm(a, rank, world, local_rank):
                 "algorithmic_bytes": alg,
                 "traffic_over_algorithmic": (traffic / alg) if traffic else None}
 
-    # ring stages (eqs. Delta2map and almfftdef): one launch per call and direction.  Algorithmic
-    # bytes per call = Delta (written or read) + maps (read or written) + the phase table once;
-    # nominal FFT work = 2.5 n log2 n flops per real ring of n pixels (one complex DFT carries two)
-    nphi_r = np.asarray(geom[0], dtype=np.float64)
-    fft_flops_map = float(2.5 * np.sum(nphi_r * np.log2(nphi_r)))
     hbm_peak = MEASURED.get("hbm_gbs") or 6800.0
 
     def ring_stages(run, steps, double_float):
-        out = {}
-        for key in ("ring_synth", "ring_anal"):
-            ms, n = run["stages"].get(key, (0.0, 0))
-            if not n:
-                continue
-            per_call_s = ms * 1e-3 / steps
-            alg = B * (plan.nrings * (L + 1) * 16 + npix * 8) + plan.nrings * (L + 1) * 16
-            gbs = alg / per_call_s / 1e9
-            tf = B * fft_flops_map / per_call_s / 1e12
-            r = {"ms_per_call": per_call_s * 1e3, "algorithmic_bytes": alg, "achieved_gbs": gbs,
-                 "hbm_peak_gbs": hbm_peak, "hbm_frac": gbs / hbm_peak,
-                 "fft_tflops_nominal": tf, "fp64_peak_tflops": peak_tf, "fp64_frac": tf / peak_tf}
-            if double_float:
-                # profiles/traffic.json records the double-float global-scratch DFTs at 16 maps per call
-                tr = traffic_from_profiles(key + "_kernel") if B == 16 else None
-                r["traffic"] = tr
-                r["traffic_over_algorithmic"] = (tr / alg) if tr else None
-            out[key] = r
-        out["note"] = ("nominal FFT flops (no Bluestein overhead) over the stage's CUDA-event time; %s" %
-                       ("double-float arithmetic on the FP32 pipe: fp64_frac is the FP64-equivalent rate"
-                        if double_float else "FP64 arithmetic"))
-        return out
+        return ring_stage_figures(run["stages"], steps, B, plan.nrings, L, npix, geom[0], hbm_peak, peak_tf,
+                                  double_float, traffic_from_profiles if double_float and B == 16 else None)
 
     head = timed(a.mode, a.steps, a.warmup, True)
     total_ms, step_ms, stages, clk = head["total_ms"], head["step_ms"], head["stages"], head["clocks"]
